@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Benchmark of the FIM black-oil linearisation path on GB300.
+
+Workload: the 100x100x20 three-phase black-oil box (200 000 cells, 3x3
+blocks, 1 372 000 stored blocks), seeded synthetic inputs.  One step is one
+pass of the whole hot path over it:
+    ocp_linearize (properties, accumulation, fluxes, wells, residual and
+    block-CSR Jacobian) + 50 x ocp_bsr_spmv (the products a Krylov solve
+    iterates on) + 1 x ocp_adjoint_vjp (all four gradients).
+Metric: Mcell FIM linearisations/s = cells x steps / time (whole job, all
+ranks).  L2 is flushed (a 512 MB write) before every step, outside the step's
+CUDA events.  Multi-GPU runs are replicas: every rank runs its own copy of the
+workload (weak scaling), no collective on the data path.
+
+``--impl reference`` times the CPU oracle (the plain FP64 numpy checker) on
+the host cores on a bounded sample of the same workload, in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SPMV = 50
+# Measured FP64 FMA rate of this GB300 pool (profiles/fp64_peak_probe.md):
+# 503 G DFMA/s = 1006 GFLOP/s.  Nominal: 1.25 TFLOP/s.
+FP64_PEAK_GFLOPS = 1006.3
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+        self.window = None
+
+    def mark(self, t0, t1):
+        """Wall-clock window (time.time()) of the timed region."""
+        self.window = (t0, t1)
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        import datetime
+        rows = []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(f[2]), float(f[3]), [n for n, v in zip(names, f[6:10])
+                                                                 if v.lower() == "active"]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        inside = rows
+        if self.window is not None:
+            inside = [r for r in rows if self.window[0] - 0.05 <= r[0] <= self.window[1] + 0.05] or rows
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "samples": len(inside), "reasons": sorted(set(n for r in inside for n in r[3]))}
+
+
+# --------------------------------------------------------------------- CPU side
+def sub_box(g, s, sx, sy, sz):
+    """The corner sub-box [0,sx) x [0,sy) x [0,sz) of the workload as a grid of
+    its own (same rock, fluid, states and the perforations inside it)."""
+    import numpy as np
+
+    from paper_2406_10862_gb300 import workloads as W
+    kk, jj, ii = np.meshgrid(np.arange(sz), np.arange(sy), np.arange(sx), indexing="ij")
+    cells = (ii + g.nx * (jj + g.ny * kk)).ravel()
+    local = {int(c): n for n, c in enumerate(cells)}
+    h = W.GridDesc(**{f: getattr(g, f) for f in g.__dataclass_fields__})
+    h.nx, h.ny, h.nz = sx, sy, sz
+    h.lnk, h.phi = g.lnk[cells], g.phi[cells]
+    h.wells = []
+    for w in g.wells:
+        inside = [local[int(c)] for c in w.cells if int(c) in local]
+        if inside:
+            h.wells.append(W.Well(kind=w.kind, phase=w.phase, p_bh=w.p_bh, rw=w.rw, skin=w.skin,
+                                  cells=np.array(inside, dtype=np.int64)))
+    st = W.State(u_new=s.u_new[:, cells], flag_new=s.flag_new[cells], u_old=s.u_old[:, cells],
+                 flag_old=s.flag_old[cells], dt=s.dt)
+    return h, st
+
+
+def oracle_sample_times(g, s, sx=100, sy=100, sz=2, n_rows=2000, seed=9):
+    """Times the CPU oracle on a bounded sample of the workload (a corner
+    sub-box, which contains a producer column) and returns seconds per cell
+    for the linearisation, per row for one SpMV and per cell for the adjoint
+    products, plus a description of the sample."""
+    import numpy as np
+
+    from oracle.linearize import linearize
+    from oracle.spmv import bsr_spmv
+
+    h, st = sub_box(g, s, sx, sy, sz)
+    nsub = h.N
+    t0 = time.perf_counter()
+    o = linearize(h, st.u_new, st.flag_new, st.u_old, st.flag_old, st.dt)
+    t_lin = (time.perf_counter() - t0) / nsub
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=nsub * 3)
+    rows = rng.choice(nsub, min(n_rows, nsub), replace=False)
+    t0 = time.perf_counter()
+    bsr_spmv(o["row_ptr"], o["col_idx"], o["val"], x, rows=rows)
+    t_spmv = (time.perf_counter() - t0) / len(rows)
+    lam = rng.normal(size=(nsub, 3))
+    t0 = time.perf_counter()
+    linearize(h, st.u_new, st.flag_new, st.u_old, st.flag_old, st.dt, mode="all", lam=lam)
+    t_vjp = (time.perf_counter() - t0) / nsub
+    desc = ("oracle (numpy, 1 thread) on the %dx%dx%d corner sub-box of the workload (%d cells): one "
+            "linearisation, one adjoint pass, and one SpMV over %d sampled rows; scaled per cell to the "
+            "step (1 linearisation + 50 SpMV + 1 adjoint)" % (sx, sy, sz, nsub, len(rows)))
+    return t_lin, t_spmv, t_vjp, desc
+
+
+def cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp):
+    return t_lin + N_SPMV * t_spmv + t_vjp
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm: every step is a bounded sample."""
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from paper_2406_10862_gb300 import workloads as W
+    g, s = W.layered_box()
+    per = []
+    desc = ""
+    # the sample shrinks with the number of steps so the run stays within minutes
+    n = args.warmup + args.steps
+    side = 100 if n <= 25 else (50 if n <= 100 else 30)
+    for k in range(n):
+        t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s, sx=side, sy=side, sz=1,
+                                                         n_rows=max(50, side * 2), seed=k)
+        if k >= args.warmup:
+            per.append(cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp))
+    sec_per_cell = statistics.mean(per)
+    value = 1e-6 / sec_per_cell
+    ms_step = sec_per_cell * g.N * 1e3
+    line = {
+        "impl": "reference", "metric": "Mcell FIM linearisations/s (FP64 residual+BSR Jacobian), % HBM roofline",
+        "value": value, "unit": "Mcell/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "layered black-oil box 100x100x20 (200000 cells, 3x3 BSR)",
+                   "step": "linearize + 50 SpMV + adjoint VJP", "global_batch": 1, "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": "Mcell/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "Mcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU side
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_10862_gb300 import build as B
+    from paper_2406_10862_gb300 import ocp, workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    B.build()
+    ocp.load()
+    g, s = W.layered_box()
+    grid = ocp.Grid(g, local_rank)
+    N, nb, nnzb = grid.N, grid.nb, grid.nnzb
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    un, fn, uo, fo = T(s.u_new.ravel()), T(s.flag_new), T(s.u_old.ravel()), T(s.flag_old)
+    r = torch.empty(nb * N, dtype=torch.float64, device=dev)
+    v = torch.empty(nnzb * nb * nb, dtype=torch.float64, device=dev)
+    ff = torch.empty(3 * nb * N, dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(11)
+    xs = [T(rng.normal(size=nb * N)) for _ in range(5)]
+    y = torch.empty(nb * N, dtype=torch.float64, device=dev)
+    lam = T(rng.normal(size=nb * N))
+    gout = {k: torch.empty(n, dtype=torch.float64, device=dev)
+            for k, n in (("unew", nb * N), ("uold", nb * N), ("lnk", N), ("phi", N))}
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size if hasattr(
+        torch.cuda.get_device_properties(dev), "L2_cache_size") else 132 * 2 ** 20
+    flush = torch.empty(max(4 * l2, 512 * 2 ** 20) // 8, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        grid.linearize(un, fn, uo, fo, s.dt, r, v, ff)
+        if ev is not None:
+            ev[1].record(stream)
+        for k in range(N_SPMV):
+            grid.spmv(v, xs[k % 5], 1.0, 0.0, y)
+        if ev is not None:
+            ev[2].record(stream)
+        grid.adjoint_vjp(un, fn, uo, fo, s.dt, v, ff, lam, out=gout)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize(dev)
+    if grid.status() != 0:
+        raise RuntimeError("device status not OK after warm-up")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)
+        w0 = time.time()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            step(evs[k])
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        clk.mark(w0, time.time())
+        time.sleep(0.1)
+    if world > 1:
+        dist.barrier()
+    st = grid.status()
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "steps": args.steps, "device_status": st}))
+        return
+    lin = [e[0].elapsed_time(e[1]) for e in evs]
+    spm = [e[1].elapsed_time(e[2]) / N_SPMV for e in evs]
+    vjp = [e[2].elapsed_time(e[3]) for e in evs]
+    ms_step = statistics.mean(a + N_SPMV * b + c for a, b, c in zip(lin, spm, vjp))
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+
+    # ---- end to end through the public API, host buffers, copies inside
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    h_un, h_fn, h_uo, h_fo = pin(s.u_new.ravel()), pin(s.flag_new), pin(s.u_old.ravel()), pin(s.flag_old)
+    h_r = torch.empty(nb * N, dtype=torch.float64).pin_memory()
+    h_y = torch.empty(nb * N, dtype=torch.float64).pin_memory()
+    h_g = torch.empty(N, dtype=torch.float64).pin_memory()
+    d_un, d_fn, d_uo, d_fo = (torch.empty_like(un), torch.empty_like(fn), torch.empty_like(uo),
+                              torch.empty_like(fo))
+    h2d = sum(t.numel() * t.element_size() for t in (h_un, h_fn, h_uo, h_fo))
+    d2h = sum(t.numel() * t.element_size() for t in (h_r, h_y, h_g))
+
+    def e2e_step():
+        d_un.copy_(h_un, non_blocking=True)
+        d_fn.copy_(h_fn, non_blocking=True)
+        d_uo.copy_(h_uo, non_blocking=True)
+        d_fo.copy_(h_fo, non_blocking=True)
+        grid.linearize(d_un, d_fn, d_uo, d_fo, s.dt, r, v, ff)
+        for k in range(N_SPMV):
+            grid.spmv(v, xs[k % 5], 1.0, 0.0, y)
+        grid.adjoint_vjp(d_un, d_fn, d_uo, d_fo, s.dt, v, ff, lam, out=gout)
+        h_r.copy_(r, non_blocking=True)
+        h_y.copy_(y, non_blocking=True)
+        h_g.copy_(gout["lnk"], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step_ms = statistics.mean(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_step_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step_ms = float(t.item())
+
+    if rank == 0:
+        spmv_ms = statistics.mean(spm)
+        flops = 2.0 * nb * nb * nnzb                               # algorithmic FP64 flops per SpMV
+        hbm_bytes = 8.0 * nb * nb * nnzb + 4.0 * nnzb + 4.0 * (N + 1) + 8.0 * nb * N * 2
+        achieved = flops / (spmv_ms * 1e-3) / 1e9
+        pk = peaks()
+        hbm_peak = pk.get("hbm_gbs")
+        line = {
+            "metric": "Mcell FIM linearisations/s (FP64 residual+BSR Jacobian), % HBM roofline",
+            "value": world * N / (ms_step * 1e-3) / 1e6, "unit": "Mcell/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "layered black-oil box 100x100x20 (200000 cells, 3x3 BSR, 1372000 blocks)",
+                       "step": "linearize + 50 SpMV + adjoint VJP", "global_batch": world,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed before every step (512 MB write outside the step events)"},
+            "phases_ms": {"linearize": statistics.mean(lin), "spmv_each": spmv_ms, "vjp": statistics.mean(vjp),
+                          "wall_timed_region_ms": wall * 1e3},
+            "roofline": {"kernel": "spmv_kernel<3,false>", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                         "peak_source": "measured FP64 FMA rate (profiles/fp64_peak_probe.md)",
+                         "traffic": None,
+                         "hbm": {"algorithmic_bytes": hbm_bytes,
+                                 "achieved_gbs": hbm_bytes / (spmv_ms * 1e-3) / 1e9,
+                                 "peak_gbs": hbm_peak,
+                                 "frac": (hbm_bytes / (spmv_ms * 1e-3) / 1e9 / hbm_peak) if hbm_peak else None}},
+            "e2e": {"value": world * N / (e2e_step_ms * 1e-3) / 1e6, "unit": "Mcell/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * (3 + N_SPMV + 1),
+            "clocks": clk.summary(),
+            "device_status": st,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s)
+            cpu = 1e-6 / cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp)
+            line["cpu_baseline"] = {"value": cpu, "unit": "Mcell/s", "cores": 1, "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="warm-up + timed steps only (no e2e, no CPU baseline): the command profiled by ncu")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local_rank = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

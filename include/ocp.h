@@ -1,0 +1,175 @@
+/*
+ * ocp.h -- C interface of the GB300 black-oil FIM linearisation library.
+ *
+ * One fully implicit (FIM) Newton linearisation of the black-oil component
+ * mass balances on a Cartesian grid with two-point fluxes, the block-CSR
+ * matrix-vector product the linear solver iterates on, and the adjoint
+ * vector-Jacobian product.  The equations are the component conservation law
+ * (eq. 1) with Darcy velocities (eq. 2) and the component amounts of eq. 4,
+ * in the black-oil closure where saturations, compositions and densities
+ * follow explicitly from the primary variables (Sec. 2.1).  The work is split
+ * the way the paper splits the reservoir: cell terms (Bulk: PVT, SAT, ROCK,
+ * ACCU -- Sec. 3.2.3), connection terms (BulkConn) and well terms (AllWells --
+ * Sec. 3.2.4), assembled into block rows of a block-CSR matrix (InternalMat of
+ * the LinearSystem module, Sec. 3.3.3) for the Newton step of Sec. 3.2.5.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units: psi, ft, mD, cP, day; oil and water in stb, gas in scf.
+ * Cells: N = nx*ny*nz in natural order c = i + nx*(j + ny*k); k grows
+ *   downward (depth of layer k is top_depth + (k + 1/2) dz).
+ * Unknowns per cell (nb of them): three-phase (p, S_w, X) with X = S_g where
+ *   flag == 0 (saturated oil) and X = R_s where flag == 1 (undersaturated
+ *   oil); two-phase oil-water (p, S_w).  p is the oil pressure.
+ * State arrays u are variable-major: u[v*N + c].  Flags are int8[N].
+ * Residual, SpMV and adjoint vectors are block-interleaved: r[nb*c + e] with
+ *   equations ordered water, oil[, gas].
+ * Jacobian: block-CSR with int32 row_ptr[N+1], col_idx[nnzb] (columns
+ *   ascending: c-nx*ny, c-nx, c-1, c, c+1, c+nx, c+nx*ny where they exist),
+ *   nnzb = 7N - 2(ny*nz + nx*nz + nx*ny), and
+ *   val[(s*nb + e)*nb + v] = dR[row, e] / du[col_idx[s], v]  (row-major
+ *   nb x nb blocks).
+ * Pointers passed to the compute calls are DEVICE pointers to memory the
+ *   caller owns (the library never frees them and keeps none after return),
+ *   on the device the grid was created on, 8-byte aligned.
+ * Compute calls are asynchronous on the given CUDA stream (NULL = the legacy
+ *   default stream).  Argument errors are returned immediately and nothing is
+ *   launched.  Errors found on the device (non-finite values, bad flags) are
+ *   sticky in the grid's status word and reported by ocp_get_status().
+ * There is no CPU fallback: every compute call runs CUDA kernels for sm_103a.
+ * Only ocp_grid_create, ocp_batch_create and their destroy calls allocate or
+ *   free device memory.
+ * ocp_last_error() returns a thread-local message describing the last failure.
+ */
+#ifndef OCP_H
+#define OCP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OCP_OK = 0,
+  OCP_ERR_INVALID_ARG = 1,  /* bad pointer, size, flag or descriptor field */
+  OCP_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  OCP_ERR_OOM = 3,          /* device allocation failed */
+  OCP_ERR_NONFINITE = 4,    /* a kernel met a NaN/Inf input or produced one */
+  OCP_ERR_TIMEOUT = 5,      /* a bounded wait expired */
+  OCP_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+} ocp_status;
+
+/* A well controlled by bottom-hole pressure (AllWells, Sec. 3.2.4).  Each
+ * perforated cell exchanges fluid with the well through Peaceman's index
+ * WI = C 2 pi k dz / (ln(r_o / rw) + skin), r_o = 0.14 sqrt(dx^2 + dy^2).
+ * A producer (kind 0) takes every phase where p > p_bh; an injector (kind 1)
+ * pushes its one phase (0 water, 2 gas) where p_bh > p, with the cell's total
+ * mobility.  A cell may be perforated by at most one well. */
+typedef struct {
+  int kind;               /* 0 producer, 1 injector */
+  int phase;              /* injected phase of an injector: 0 water, 2 gas */
+  double p_bh;            /* bottom-hole pressure, psi */
+  double rw;              /* wellbore radius, ft (> 0) */
+  double skin;
+  int nperf;              /* number of perforated cells */
+  const int64_t* cells;   /* HOST array [nperf] of natural cell indices */
+} ocp_well;
+
+/* Grid, rock, fluid and wells: the statement of the problem (Sec. 2.1 and the
+ * Bulk sub-modules of Sec. 3.2.3).  All pointers are HOST pointers; the
+ * library copies what it needs and keeps none of them. */
+typedef struct {
+  int nx, ny, nz;                 /* cells per direction, each >= 1 */
+  double dx, dy, dz;              /* cell size, ft (> 0) */
+  double top_depth;               /* depth of the top face, ft */
+  int nphase;                     /* 3 (black oil, 3x3 blocks) or 2 (oil-water, 2x2) */
+  const double* lnk;              /* [N] ln(k_x / mD); k_y = k_x, k_z = kz_over_kx k_x */
+  const double* phi;              /* [N] porosity at p_ref (> 0) */
+  double kz_over_kx, cr, p_ref;   /* rock: phi(p) = phi (1 + cr (p - p_ref)) */
+  int nrow;                       /* PVT rows, 2..64, tab_p strictly increasing */
+  const double *tab_p, *tab_Bo, *tab_Bg, *tab_Rs, *tab_muo, *tab_mug;
+  /* water b_w = bw_ref (1 + cw (p - p_ref)), constant viscosity muw;
+   * surface densities (lb/ft^3); undersaturated oil compressibility co_under
+   * and viscosibility cmu_under (1/psi) */
+  double bw_ref, cw, muw, rho_osc, rho_gsc, rho_wsc, co_under, cmu_under;
+  /* Corey end points and exponents (>= 1), Stone II with kro_cw, and the
+   * maximum oil-water and gas-oil capillary pressures (psi) */
+  double swc, sorw, sorg, sgc, nw, now, ng, nog, krw_max, krg_max, kro_cw, pcow_max, pcgo_max;
+  int nwell;
+  const ocp_well* wells;          /* HOST array [nwell] */
+} ocp_grid_desc;
+
+typedef struct ocp_grid ocp_grid;     /* opaque, library-owned */
+
+/* Set-up (Solver::Setup analogue, Sec. 3.3.1): validates the descriptor,
+ * selects `device`, allocates the grid's device data (transmissibilities,
+ * pore volumes, well indices, the block-CSR pattern, PVT constants) and
+ * fills it.  Returns OCP_ERR_INVALID_ARG for an inconsistent descriptor,
+ * OCP_ERR_OOM / OCP_ERR_CUDA on device failure (nothing leaks). */
+ocp_status ocp_grid_create(const ocp_grid_desc* desc, int device, ocp_grid** out);
+ocp_status ocp_grid_destroy(ocp_grid* grid);      /* NULL is accepted */
+
+/* Sizes: number of cells, block size nb, number of stored blocks. */
+ocp_status ocp_grid_info(const ocp_grid* grid, int64_t* ncell, int* nb, int64_t* nnzb);
+
+/* Device pointers to the grid's block-CSR pattern (owned by the grid, valid
+ * until ocp_grid_destroy). */
+ocp_status ocp_bsr_pattern(const ocp_grid* grid, const int32_t** row_ptr, const int32_t** col_idx);
+
+/* One FIM linearisation (Sec. 3.2.5 steps 1 and 3: property update and
+ * Jacobian assembly).  Computes, for the backward-Euler step of length dt
+ * (days, > 0) from (u_old, flag_old) to (u_new, flag_new):
+ *   residual[nb*N]   R = (V/5.614583/dt)(m(u_new) - m(u_old)) + sum of
+ *                    outgoing upwinded TPFA fluxes - well sources;
+ *   bsr_val[nnzb*nb*nb]  J = dR/du_new in the layout above;
+ *   face_flux[3*nb*N] (may be NULL) component fluxes across the +x, +y, +z
+ *                    face of every cell: face_flux[(d*nb + e)*N + c], zero
+ *                    where the face does not exist (input of the adjoint).
+ * Device-detected NaN/Inf in the state, or a flag other than 0/1, sets the
+ * sticky status OCP_ERR_NONFINITE / OCP_ERR_INVALID_ARG. */
+ocp_status ocp_linearize(ocp_grid* grid, const double* u_new, const int8_t* flag_new,
+                         const double* u_old, const int8_t* flag_old, double dt,
+                         double* residual, double* bsr_val, double* face_flux, void* cuda_stream);
+
+/* Block-CSR product of the linear solver (LinearSystem, Sec. 3.3.3):
+ * y = alpha * A x + beta * y, or with transpose != 0, y = alpha * A^T x +
+ * beta * y.  A is bsr_val on the grid's pattern; x and y are block-
+ * interleaved [nb*N] device vectors and must not overlap.  beta == 0 does
+ * not read y (so y may hold NaNs). */
+ocp_status ocp_bsr_spmv(const ocp_grid* grid, const double* bsr_val, double alpha, const double* x,
+                        double beta, double* y, int transpose, void* cuda_stream);
+
+/* Adjoint vector-Jacobian products of the residual of ocp_linearize (the
+ * derivative of eqs. 1, 2 and 4 with respect to the model parameters and the
+ * states), for a block-interleaved multiplier lambda[nb*N]:
+ *   g_unew[nb*N]  (J^T lambda), variable-major like u;
+ *   g_uold[nb*N]  (dR/du_old)^T lambda, variable-major;
+ *   g_lnk[N]      (dR/d ln k)^T lambda  (through T and WI);
+ *   g_phi[N]      (dR/d phi)^T lambda   (through the pore volume).
+ * bsr_val and face_flux must be the outputs of ocp_linearize at the same
+ * states and dt.  Any g_* may be NULL (not computed).  Outputs are
+ * overwritten, not accumulated. */
+ocp_status ocp_adjoint_vjp(ocp_grid* grid, const double* u_new, const int8_t* flag_new,
+                           const double* u_old, const int8_t* flag_old, double dt,
+                           const double* bsr_val, const double* face_flux, const double* lambda,
+                           double* g_unew, double* g_uold, double* g_lnk, double* g_phi,
+                           void* cuda_stream);
+
+/* Surface rates of every well at a state (AllWells, Sec. 3.2.4):
+ * q[w*nb + e], component e of well w summed over its perforations,
+ * positive into the reservoir (stb/day; scf/day for gas). */
+ocp_status ocp_well_rates(ocp_grid* grid, const double* u, const int8_t* flag, double* q,
+                          void* cuda_stream);
+
+/* Synchronises the stream, then returns and clears the grid's sticky device
+ * status (OCP_OK if no kernel reported a problem since the last call). */
+ocp_status ocp_get_status(ocp_grid* grid, void* cuda_stream);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* ocp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCP_H */

@@ -157,6 +157,8 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
     val = np.zeros((len(col_idx), nb, nb))
     valm = np.zeros((len(col_idx), nb, nb))
     gw = np.zeros((N, L)) if lam is not None else None
+    gwm = np.zeros((N, L)) if lam is not None else None
+    alam = np.abs(lam) if lam is not None else None
     cells = np.arange(N)
     diag = row_ptr[:-1] + slot[3]
 
@@ -173,11 +175,13 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
         add_block(diag, e, acc[e].g[:, :nv], acc[e].gm[:, :nv], 1.0)
         if gw is not None:
             gw += lam[:, e:e + 1] * acc[e].g
+            gwm += alam[:, e:e + 1] * acc[e].gm
 
     # ---- connection fluxes (BulkConn): two-point, phase-upwinded
     z = depth(spec)
     phases = ["w", "o", "g"][:nb]
     face_flux = np.zeros((3, nb, N))
+    face_flux_mag = np.zeros((3, nb, N))
     face_dphi = {}
     for d in range(3):
         fi, fj = face_pairs(spec, d)
@@ -210,6 +214,7 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
         for e in range(nb):
             q = comp[e]
             face_flux[d, e, fi] = q.v
+            face_flux_mag[d, e, fi] = q.m
             add_rows(fi, e, q, 1.0)
             add_rows(fj, e, q, -1.0)
             gi, gj = q.g[:, :nv], q.g[:, L:L + nv]
@@ -222,6 +227,9 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
                 w = (lam[fi, e] - lam[fj, e])[:, None]
                 np.add.at(gw, fi, w * q.g[:, :L])
                 np.add.at(gw, fj, w * q.g[:, L:])
+                wm = (alam[fi, e] + alam[fj, e])[:, None]
+                np.add.at(gwm, fi, wm * q.gm[:, :L])
+                np.add.at(gwm, fj, wm * q.gm[:, L:])
 
     # ---- wells (AllWells): bottom-hole-pressure controlled perforations
     well_q = np.zeros((N, nb))
@@ -254,15 +262,21 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
             add_block(diag[cells_w], e, q.g[:, :nv], q.gm[:, :nv], -1.0)
             if gw is not None:
                 np.add.at(gw, cells_w, -lam[cells_w, e:e + 1] * q.g)
+                np.add.at(gwm, cells_w, alam[cells_w, e:e + 1] * q.gm)
 
     out = {
         "R": R, "R_mag": Rm, "row_ptr": row_ptr, "col_idx": col_idx,
         "val": val, "val_mag": valm, "acc": np.stack([a.v for a in acc], axis=1),
-        "well_q": well_q, "face_flux": face_flux, "face_dphi": face_dphi,
+        "well_q": well_q, "face_flux": face_flux, "face_flux_mag": face_flux_mag,
+        "face_dphi": face_dphi,
     }
     if gw is not None:
         out["g_unew"] = gw[:, :nv].T.copy()
         out["g_uold"] = gw[:, nv:2 * nv].T.copy()
         out["g_lnk"] = gw[:, 2 * nv].copy()
         out["g_phi"] = gw[:, 2 * nv + 1].copy()
+        out["g_unew_mag"] = gwm[:, :nv].T.copy()
+        out["g_uold_mag"] = gwm[:, nv:2 * nv].T.copy()
+        out["g_lnk_mag"] = gwm[:, 2 * nv].copy()
+        out["g_phi_mag"] = gwm[:, 2 * nv + 1].copy()
     return out

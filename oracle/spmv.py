@@ -12,16 +12,20 @@ from __future__ import annotations
 import numpy as np
 
 
-def bsr_spmv(row_ptr, col_idx, val, x, alpha=1.0, beta=0.0, y=None, transpose=False):
+def bsr_spmv(row_ptr, col_idx, val, x, alpha=1.0, beta=0.0, y=None, transpose=False, rows=None):
     """y <- alpha * A x + beta * y  (or A^T x).  Also returns the magnitude
-    |alpha| |A| |x| + |beta| |y| used as the per-entry tolerance scale."""
+    |alpha| |A| |x| + |beta| |y| used as the per-entry tolerance scale.
+    With ``rows`` given (non-transposed only), only those block rows are
+    computed; the other entries of the result are left at zero."""
     nb = val.shape[1]
     N = len(row_ptr) - 1
     X = np.asarray(x, dtype=np.float64).reshape(N, nb)
     Y0 = np.zeros((N, nb)) if y is None else np.asarray(y, dtype=np.float64).reshape(N, nb)
     acc = np.zeros((N, nb))
     mag = np.zeros((N, nb))
-    for r in range(N):
+    if rows is not None and transpose:
+        raise ValueError("row sampling is for the plain product only")
+    for r in (range(N) if rows is None else rows):
         for s in range(row_ptr[r], row_ptr[r + 1]):
             c = col_idx[s]
             blk = val[s]

@@ -1,0 +1,22 @@
+// Launchers shared between the translation units of the library.
+#pragma once
+#include "ocp_internal.cuh"
+
+namespace ocp {
+
+int64_t linearize_scratch_doubles(int64_t N);
+cudaError_t launch_linearize(const ocp_grid* g, const double* u_new, const int8_t* f_new,
+                             const double* u_old, const int8_t* f_old, double dt, double* res,
+                             double* val, double* face_flux, cudaStream_t s);
+cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, const double* x, double beta,
+                        double* y, int transpose, cudaStream_t s);
+cudaError_t launch_vjp(const ocp_grid* g, const double* u_new, const int8_t* f_new, const double* u_old,
+                       const int8_t* f_old, double dt, const double* val, const double* face_flux,
+                       const double* lam, double* g_unew, double* g_uold, double* g_lnk, double* g_phi,
+                       cudaStream_t s);
+cudaError_t launch_well_rates(const ocp_grid* g, const double* u, const int8_t* flag, double* q,
+                              cudaStream_t s);
+cudaError_t launch_setup(ocp_grid* g, const double* d_lnk, double dx, double dy, double dz,
+                         double kz_over_kx, cudaStream_t s);
+
+}  // namespace ocp

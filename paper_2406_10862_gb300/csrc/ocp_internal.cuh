@@ -1,0 +1,482 @@
+// Internal definitions of the GB300 black-oil FIM linearisation library.
+//
+// Everything here is FP64.  On GB300 (sm_103) the FP64 pipe issues about two
+// DFMA per SM clock -- 1/74 of the FP32 rate -- and an FP64 compare costs as
+// much as an FMA, so the device code below is written to spend as few FP64
+// instructions as possible: branch decisions on doubles are taken on their
+// bit patterns with integer instructions, every per-grid constant (reciprocal
+// normalisations, table slopes, transmissibilities, well indices) is
+// precomputed once at set-up, and horizontal faces skip the gravity term,
+// whose depth difference is zero there.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ocp.h"
+
+namespace ocp {
+
+constexpr int kMaxRows = 64;           // PVT table rows
+constexpr double kRbFt3 = 5.614583;    // ft^3 per reservoir barrel
+constexpr double kDarcy = 0.001127;    // rb cP / (day psi mD ft)
+constexpr double kGrav = 1.0 / 144.0;  // psi per (lb/ft^3 ft)
+
+// Sticky device status bits (ocp_get_status maps them to ocp_status).
+enum : int { kStatNonFinite = 1, kStatBadFlag = 2, kStatTimeout = 4 };
+
+// Preprocessed PVT table: knots and, per linear piece k, value and slope of
+// b_o = 1/B_o, 1/mu_o, b_g = 1/B_g, 1/mu_g and R_s versus p, plus the inverse
+// piece p(R_s) for undersaturated oil.  Filled on the host at set-up.
+struct Table {
+  int nrow;
+  double p[kMaxRows];
+  double rs[kMaxRows];
+  double y[5][kMaxRows];       // 0 b_o, 1 imu_o, 2 b_g, 3 imu_g, 4 R_s at the knots
+  double s[5][kMaxRows];       // slope of piece k
+  double q[kMaxRows];          // dp/dR_s of piece k (inverse of R_s(p))
+  long long pkey[kMaxRows];    // order-preserving integer keys of p and R_s knots
+  long long rskey[kMaxRows];
+};
+
+// Per-grid scalar constants, passed to kernels by value.
+struct Params {
+  int nx, ny, nz, nb;
+  long long N, nxy;
+  double dz;
+  double p_ref, cr, bw_ref, cw, imu_w;
+  double rho_osc, rho_wsc, cg;            // cg = rho_gsc / 5.614583
+  double co, cmu;
+  double swc, sorw, sorg, sgc;
+  double inv_w, inv_g, inv_og;            // 1/(1-swc-sorw), 1/(1-swc-sgc-sorg), 1/(1-swc-sorg)
+  double nw, now, ng, nog;                // Corey exponents
+  int sq_w, sq_ow, sq_g, sq_og;           // exponent == 2 (use a product, not pow)
+  double krw_max, krg_max, kc;
+  double pcow_max, pcgo_max;
+  double grav_dz;                         // 0.5 * g * dz: half the potential head per unit density
+  double vol_rb;                          // cell bulk volume in rb
+};
+
+// Well perforation data on the device (one entry per perforated cell).
+struct Perf {
+  int cell;
+  int well;
+  int kind;       // 0 producer, 1 injector
+  int phase;      // injected phase (0 water, 2 gas)
+  double wi;      // Peaceman index including k of the cell
+  double p_bh;
+};
+
+}  // namespace ocp
+
+// The opaque handle of the C interface.
+struct ocp_grid {
+  int device;
+  ocp::Params prm;
+  ocp::Table* d_table;       // device copy of the table
+  ocp::Table h_table;
+  int64_t nnzb;
+  int32_t* d_row_ptr;
+  int32_t* d_col_idx;
+  int32_t* d_mirror;         // index of block (col,row) for block (row,col)
+  double* d_trans;           // [3][N] transmissibility of the +x,+y,+z face (0 outside)
+  double* d_wlnk;            // [3][N] dlnT/dln k_i of the +face for its lower cell
+  double* d_phi;             // [N] reference porosity
+  int32_t* d_perf_of_cell;   // [N] perforation index or -1
+  ocp::Perf* d_perf;         // [nperf]
+  int nperf;
+  int nwell;
+  int32_t* d_well_first;     // [nwell+1] perforations of well w: well_first[w] .. well_first[w+1]
+  int* d_status;             // sticky device status word
+  double* d_scratch;         // per-cell scratch of the linearisation
+  int64_t scratch_doubles;
+};
+
+namespace ocp {
+
+// ---------------------------------------------------------------- bit tricks
+// Order-preserving signed integer key of a double (total order on non-NaN).
+__host__ __device__ inline long long dkey(double x) {
+#ifdef __CUDA_ARCH__
+  long long b = __double_as_longlong(x);
+#else
+  long long b;
+  __builtin_memcpy(&b, &x, 8);
+#endif
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+// x >= 0 (true for +0 and -0), without an FP64 compare.
+__device__ __forceinline__ bool nonneg(double x) { return dkey(x) >= dkey(-0.0); }
+// x > 0 strictly.
+__device__ __forceinline__ bool positive(double x) { return dkey(x) > 0; }
+__device__ __forceinline__ bool finite(double x) {
+  return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff;
+}
+__device__ __forceinline__ double sel(bool c, double a, double b) { return c ? a : b; }
+
+// Largest k <= nrow-2 with key[k] <= xk (binary search on integer keys).
+__device__ __forceinline__ int segment(const long long* key, int nrow, long long xk) {
+  int lo = 0, hi = nrow - 2;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (key[mid] <= xk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Power with a constant exponent >= 1 and its derivative; exponent 2 uses a
+// product.  s is already clamped to [0, 1].
+__device__ __forceinline__ void cpow(double s, double n, int sq, double& v, double& d) {
+  if (sq) { v = s * s; d = s + s; }
+  else { v = pow(s, n); d = n * pow(s, n - 1.0); }
+}
+
+// Clamp a normalised saturation to [0, 1]: outside, value clamped and slope 0.
+__device__ __forceinline__ void clamp01(double& s, double& ds) {
+  if (!nonneg(s)) { s = 0.0; ds = 0.0; }
+  else if (dkey(s) > dkey(1.0)) { s = 1.0; ds = 0.0; }
+}
+
+// ------------------------------------------------------------ cell quantities
+// Quantities of one cell that the face and well terms need, with derivatives
+// with respect to the cell's own unknowns (p, S_w, X).  Two-phase cells use
+// the water/oil entries only.
+struct CellQ {
+  double p, pw, pg;            // phase pressures (p_o = p)
+  double dpw_sw, dpg_x;        // the only non-unit pressure derivatives
+  double rw, rw_p;             // densities
+  double ro, ro_p, ro_x;
+  double rg, rg_p;
+  double lw, lw_p, lw_sw;      // mobilities k_r b / mu
+  double lo, lo_p, lo_sw, lo_x;
+  double lg, lg_p, lg_x;
+  double rs, rs_p, rs_x;       // dissolved gas-oil ratio
+};
+
+// Extra per-cell quantities for accumulation and injectors.
+struct CellAux {
+  double m[3], m_p[3], m_sw[3], m_x[3];    // phi S b per component, with derivatives
+  double mob, mob_p, mob_sw, mob_x;         // total mobility sum k_r / mu
+  double bw, bw_p, bg, bg_p;                // injected-phase b and its p-derivative
+};
+
+// PVT, rock, Corey / Stone II, capillary pressure, densities and mobilities
+// of one cell (Bulk: PVT, SAT, ROCK modules, Sec. 3.2.3).
+template <int NB, bool AUX>
+__device__ __forceinline__ void cell_quantities(const Params& P, const Table& T, double p, double sw,
+                                                double x, int flag, double phi_ref, CellQ& q,
+                                                CellAux& a) {
+  const double t = p - P.p_ref;
+  // water
+  const double bw = P.bw_ref * fma(P.cw, t, 1.0);
+  const double bw_p = P.bw_ref * P.cw;
+  // oil (and gas) from the table
+  double bo, bo_p, bo_x, imo, imo_p, imo_x, rs, rs_p, rs_x, sg, sg_x;
+  double bg = 0.0, bg_p = 0.0, img = 0.0, img_p = 0.0;
+  const int kp = segment(T.pkey, T.nrow, dkey(p));
+  const double dpk = p - T.p[kp];
+  if (NB == 3 && flag == 1) {
+    const int kr = segment(T.rskey, T.nrow, dkey(x));
+    const double pb = fma(x - T.rs[kr], T.q[kr], T.p[kr]);
+    const double pb_x = T.q[kr];
+    const double dpb = pb - T.p[kr];
+    const double dp = p - pb;
+    const double bsat = fma(dpb, T.s[0][kr], T.y[0][kr]);
+    const double isat = fma(dpb, T.s[1][kr], T.y[1][kr]);
+    const double fb = fma(P.co, dp, 1.0);
+    const double fm = fma(-P.cmu, dp, 1.0);
+    bo = bsat * fb;
+    bo_p = bsat * P.co;
+    bo_x = (T.s[0][kr] * fb - bsat * P.co) * pb_x;
+    imo = isat * fm;
+    imo_p = -isat * P.cmu;
+    imo_x = (T.s[1][kr] * fm + isat * P.cmu) * pb_x;
+    rs = x; rs_p = 0.0; rs_x = 1.0;
+    sg = 0.0; sg_x = 0.0;
+  } else {
+    bo = fma(dpk, T.s[0][kp], T.y[0][kp]);
+    bo_p = T.s[0][kp]; bo_x = 0.0;
+    imo = fma(dpk, T.s[1][kp], T.y[1][kp]);
+    imo_p = T.s[1][kp]; imo_x = 0.0;
+    if (NB == 3) {
+      rs = fma(dpk, T.s[4][kp], T.y[4][kp]);
+      rs_p = T.s[4][kp];
+    } else {
+      rs = 0.0; rs_p = 0.0;
+    }
+    rs_x = 0.0;
+    sg = (NB == 3) ? x : 0.0;
+    sg_x = (NB == 3) ? 1.0 : 0.0;
+  }
+  if (NB == 3) {
+    bg = fma(dpk, T.s[2][kp], T.y[2][kp]);
+    bg_p = T.s[2][kp];
+    img = fma(dpk, T.s[3][kp], T.y[3][kp]);
+    img_p = T.s[3][kp];
+  }
+
+  // relative permeabilities (Corey; Stone II for oil with three phases)
+  double s_w = (sw - P.swc) * P.inv_w, s_w_d = P.inv_w;
+  clamp01(s_w, s_w_d);
+  double s_ow = (1.0 - sw - P.sorw) * P.inv_w, s_ow_d = -P.inv_w;
+  clamp01(s_ow, s_ow_d);
+  double pw_, dw_, pow_, dow_;
+  cpow(s_w, P.nw, P.sq_w, pw_, dw_);
+  cpow(s_ow, P.now, P.sq_ow, pow_, dow_);
+  const double krw = P.krw_max * pw_;
+  const double krw_sw = P.krw_max * dw_ * s_w_d;
+  double kro, kro_sw, kro_sg = 0.0, krg = 0.0, krg_sg = 0.0, s_g = 0.0, s_g_d = 0.0;
+  if (NB == 3) {
+    s_g = (sg - P.sgc) * P.inv_g;
+    s_g_d = P.inv_g;
+    clamp01(s_g, s_g_d);
+    double s_og = (1.0 - sg - P.swc - P.sorg) * P.inv_og, s_og_d = -P.inv_og;
+    clamp01(s_og, s_og_d);
+    double pg_, dg_, pog_, dog_;
+    cpow(s_g, P.ng, P.sq_g, pg_, dg_);
+    cpow(s_og, P.nog, P.sq_og, pog_, dog_);
+    krg = P.krg_max * pg_;
+    krg_sg = P.krg_max * dg_ * s_g_d;
+    // k_ro = kc [(k_row/kc + k_rw)(k_rog/kc + k_rg) - (k_rw + k_rg)], k_row/kc = s_ow^n
+    const double A = pow_ + krw;
+    const double A_sw = dow_ * s_ow_d + krw_sw;
+    const double B = pog_ + krg;
+    const double B_sg = dog_ * s_og_d + krg_sg;
+    kro = P.kc * fma(A, B, -(krw + krg));
+    kro_sw = P.kc * fma(A_sw, B, -krw_sw);
+    kro_sg = P.kc * fma(A, B_sg, -krg_sg);
+    if (!nonneg(kro)) { kro = 0.0; kro_sw = 0.0; kro_sg = 0.0; }
+  } else {
+    kro = P.kc * pow_;
+    kro_sw = P.kc * dow_ * s_ow_d;
+  }
+  const double kro_x = kro_sg * sg_x;
+  const double krg_x = krg_sg * sg_x;
+
+  // capillary pressures: p_w = p - Pc_ow(S_w), p_g = p + Pc_go(S_g)
+  const double omw = 1.0 - s_w;
+  q.p = p;
+  q.pw = p - P.pcow_max * (omw * omw);
+  q.dpw_sw = 2.0 * P.pcow_max * omw * s_w_d;
+  if (NB == 3) {
+    q.pg = p + P.pcgo_max * (s_g * s_g);
+    q.dpg_x = 2.0 * P.pcgo_max * s_g * s_g_d * sg_x;
+  }
+
+  // densities
+  q.rw = bw * P.rho_wsc;
+  q.rw_p = bw_p * P.rho_wsc;
+  const double ro0 = fma(rs, P.cg, P.rho_osc);
+  q.ro = ro0 * bo;
+  q.ro_p = fma(P.cg * rs_p, bo, ro0 * bo_p);
+  q.ro_x = fma(P.cg * rs_x, bo, ro0 * bo_x);
+  if (NB == 3) {
+    q.rg = bg * P.cg;
+    q.rg_p = bg_p * P.cg;
+  }
+
+  // mobilities lambda = k_r * b / mu
+  const double bmw = bw * P.imu_w;
+  q.lw = krw * bmw;
+  q.lw_p = krw * (bw_p * P.imu_w);
+  q.lw_sw = krw_sw * bmw;
+  const double bmo = bo * imo;
+  const double bmo_p = fma(bo_p, imo, bo * imo_p);
+  const double bmo_x = fma(bo_x, imo, bo * imo_x);
+  q.lo = kro * bmo;
+  q.lo_p = kro * bmo_p;
+  q.lo_sw = kro_sw * bmo;
+  q.lo_x = fma(kro_x, bmo, kro * bmo_x);
+  if (NB == 3) {
+    const double bmg = bg * img;
+    q.lg = krg * bmg;
+    q.lg_p = krg * fma(bg_p, img, bg * img_p);
+    q.lg_x = krg_x * bmg;
+    q.rs = rs; q.rs_p = rs_p; q.rs_x = rs_x;
+  }
+
+  if (AUX) {
+    // component amounts per bulk volume (eq. 4, black-oil form)
+    const double fr = fma(P.cr, t, 1.0);
+    const double phi = phi_ref * fr;
+    const double phi_p = phi_ref * P.cr;
+    const double so = (NB == 3) ? (1.0 - sw - sg) : (1.0 - sw);
+    const double so_x = -sg_x;
+    a.m[0] = phi * sw * bw;
+    a.m_p[0] = fma(phi_p * sw, bw, phi * sw * bw_p);
+    a.m_sw[0] = phi * bw;
+    a.m_x[0] = 0.0;
+    const double sob = so * bo;
+    a.m[1] = phi * sob;
+    a.m_p[1] = fma(phi_p, sob, phi * so * bo_p);
+    a.m_sw[1] = -phi * bo;
+    a.m_x[1] = phi * fma(so_x, bo, so * bo_x);
+    if (NB == 3) {
+      const double G = fma(sg, bg, rs * sob);
+      const double G_p = fma(sg, bg_p, fma(rs_p, sob, rs * so * bo_p));
+      const double G_sw = -rs * bo;
+      const double G_x = fma(sg_x, bg, fma(rs_x, sob, rs * fma(so_x, bo, so * bo_x)));
+      a.m[2] = phi * G;
+      a.m_p[2] = fma(phi_p, G, phi * G_p);
+      a.m_sw[2] = phi * G_sw;
+      a.m_x[2] = phi * G_x;
+      a.mob = fma(krw, P.imu_w, fma(kro, imo, krg * img));
+      a.mob_p = fma(kro, imo_p, krg * img_p);
+      a.mob_sw = fma(krw_sw, P.imu_w, kro_sw * imo);
+      a.mob_x = fma(kro_x, imo, fma(kro, imo_x, krg_x * img));
+      a.bg = bg; a.bg_p = bg_p;
+    } else {
+      a.mob = fma(krw, P.imu_w, kro * imo);
+      a.mob_p = kro * imo_p;
+      a.mob_sw = fma(krw_sw, P.imu_w, kro_sw * imo);
+      a.mob_x = 0.0;
+    }
+    a.bw = bw; a.bw_p = bw_p;
+  }
+}
+
+// Component amounts (values only) at the old time level.
+template <int NB>
+__device__ __forceinline__ void cell_masses(const Params& P, const Table& T, double p, double sw,
+                                            double x, int flag, double phi_ref, double* m) {
+  CellQ q{};
+  CellAux a{};
+  cell_quantities<NB, true>(P, T, p, sw, x, flag, phi_ref, q, a);
+  for (int e = 0; e < NB; ++e) m[e] = a.m[e];
+}
+
+// ---------------------------------------------------------------- face flux
+// Flux of every component across one face (i -> j, j the + neighbour) and
+// its derivatives with respect to both cells' unknowns (BulkConn, Sec. 3.2.4;
+// Darcy's law eq. 2 in two-point form, phase-upwinded).
+template <int NB>
+struct FaceOut {
+  double F[NB];
+  double di[NB][NB];   // dF_e / du_i[v]
+  double dj[NB][NB];   // dF_e / du_j[v]
+};
+
+// One phase: F = T lambda_up dphi, dphi = (pa_i - pa_j) - gbar (z_i - z_j),
+// gbar = g (rho_i + rho_j)/2.  `hz` = 0.5 g (z_i - z_j) (zero on horizontal
+// faces, where GRAV is false and the gravity arithmetic is skipped).
+// Outputs the flux and its derivatives in the local variables
+// (p, S_w, X) of i and j.
+template <bool GRAV>
+__device__ __forceinline__ void phase_flux(double T, double hz, double pa_i, double pa_j,
+                                           double rho_i, double rho_j,
+                                           // d pa / d(p, S_w, X) of each side
+                                           double pa_sw_i, double pa_x_i, double pa_sw_j, double pa_x_j,
+                                           // d rho / d(p, X) of each side
+                                           double rho_p_i, double rho_x_i, double rho_p_j, double rho_x_j,
+                                           // lambda and derivatives of each side
+                                           double l_i, double l_p_i, double l_sw_i, double l_x_i,
+                                           double l_j, double l_p_j, double l_sw_j, double l_x_j,
+                                           double& F, double* di, double* dj, bool& up_i) {
+  double dphi = pa_i - pa_j;
+  if (GRAV) dphi = fma(-(rho_i + rho_j), hz, dphi);
+  up_i = nonneg(dphi);
+  const double lu = sel(up_i, l_i, l_j);
+  const double Tl = T * lu;
+  const double Td = T * dphi;
+  F = Tl * dphi;
+  // derivative of dphi
+  double dp_i = 1.0, dp_j = -1.0, dx_i = pa_x_i, dx_j = -pa_x_j;
+  if (GRAV) {
+    dp_i = fma(-rho_p_i, hz, 1.0);
+    dp_j = fma(-rho_p_j, hz, -1.0);
+    dx_i = fma(-rho_x_i, hz, dx_i);
+    dx_j = fma(-rho_x_j, hz, dx_j);
+  }
+  // upwind mobility derivatives go to the upstream side only
+  const double ulp = Td * sel(up_i, l_p_i, l_p_j);
+  const double ulsw = Td * sel(up_i, l_sw_i, l_sw_j);
+  const double ulx = Td * sel(up_i, l_x_i, l_x_j);
+  di[0] = fma(Tl, dp_i, sel(up_i, ulp, 0.0));
+  dj[0] = fma(Tl, dp_j, sel(up_i, 0.0, ulp));
+  di[1] = fma(Tl, pa_sw_i, sel(up_i, ulsw, 0.0));
+  dj[1] = fma(-Tl, pa_sw_j, sel(up_i, 0.0, ulsw));
+  di[2] = fma(Tl, dx_i, sel(up_i, ulx, 0.0));
+  dj[2] = fma(Tl, dx_j, sel(up_i, 0.0, ulx));
+}
+
+template <int NB, bool GRAV>
+__device__ __forceinline__ void face_terms(double T, double hz, const CellQ& a, const CellQ& b,
+                                          FaceOut<NB>& o) {
+  double dw_i[3], dw_j[3], do_i[3], do_j[3];
+  bool up_w, up_o;
+  // water: p_w = p - Pc_ow(S_w); rho_w depends on p only
+  phase_flux<GRAV>(T, hz, a.pw, b.pw, a.rw, b.rw, a.dpw_sw, 0.0, b.dpw_sw, 0.0, a.rw_p, 0.0, b.rw_p, 0.0,
+                   a.lw, a.lw_p, a.lw_sw, 0.0, b.lw, b.lw_p, b.lw_sw, 0.0, o.F[0], dw_i, dw_j, up_w);
+  // oil: p_o = p; rho_o depends on p and X
+  phase_flux<GRAV>(T, hz, a.p, b.p, a.ro, b.ro, 0.0, 0.0, 0.0, 0.0, a.ro_p, a.ro_x, b.ro_p, b.ro_x,
+                   a.lo, a.lo_p, a.lo_sw, a.lo_x, b.lo, b.lo_p, b.lo_sw, b.lo_x, o.F[1], do_i, do_j, up_o);
+  for (int v = 0; v < NB; ++v) {
+    o.di[0][v] = dw_i[v]; o.dj[0][v] = dw_j[v];
+    o.di[1][v] = do_i[v]; o.dj[1][v] = do_j[v];
+  }
+  if (NB == 3) {
+    double dg_i[3], dg_j[3];
+    bool up_g;
+    phase_flux<GRAV>(T, hz, a.pg, b.pg, a.rg, b.rg, 0.0, a.dpg_x, 0.0, b.dpg_x, a.rg_p, 0.0, b.rg_p, 0.0,
+                     a.lg, a.lg_p, 0.0, a.lg_x, b.lg, b.lg_p, 0.0, b.lg_x, o.F[NB - 1], dg_i, dg_j, up_g);
+    // gas component: free gas plus gas dissolved in the upstream oil
+    const double rsu = sel(up_o, a.rs, b.rs);
+    const double Fo = o.F[1];
+    o.F[NB - 1] = fma(rsu, Fo, o.F[NB - 1]);
+    const double frp = Fo * sel(up_o, a.rs_p, b.rs_p);
+    const double frx = Fo * sel(up_o, a.rs_x, b.rs_x);
+    o.di[NB - 1][0] = fma(rsu, do_i[0], dg_i[0]) + sel(up_o, frp, 0.0);
+    o.dj[NB - 1][0] = fma(rsu, do_j[0], dg_j[0]) + sel(up_o, 0.0, frp);
+    o.di[NB - 1][1] = fma(rsu, do_i[1], dg_i[1]);
+    o.dj[NB - 1][1] = fma(rsu, do_j[1], dg_j[1]);
+    o.di[NB - 1][2] = fma(rsu, do_i[2], dg_i[2]) + sel(up_o, frx, 0.0);
+    o.dj[NB - 1][2] = fma(rsu, do_j[2], dg_j[2]) + sel(up_o, 0.0, frx);
+  }
+}
+
+// ---------------------------------------------------------------- wells
+// Source of every component at a perforated cell (positive into the
+// reservoir) and its derivatives (AllWells, Sec. 3.2.4).
+template <int NB>
+__device__ __forceinline__ void well_source(const Perf& w, const CellQ& q, const CellAux& a,
+                                            double* src, double (*d)[3]) {
+  for (int e = 0; e < NB; ++e) {
+    src[e] = 0.0;
+    d[e][0] = d[e][1] = d[e][2] = 0.0;
+  }
+  if (w.kind == 0) {
+    const double drive = q.p - w.p_bh;
+    if (!positive(drive)) return;
+    const double g = w.p_bh - q.p;   // negative
+    // q_a = WI lambda_a (p_bh - p)
+    src[0] = w.wi * q.lw * g;
+    d[0][0] = w.wi * fma(q.lw_p, g, -q.lw);
+    d[0][1] = w.wi * q.lw_sw * g;
+    src[1] = w.wi * q.lo * g;
+    d[1][0] = w.wi * fma(q.lo_p, g, -q.lo);
+    d[1][1] = w.wi * q.lo_sw * g;
+    d[1][2] = w.wi * q.lo_x * g;
+    if (NB == 3) {
+      const double qg = w.wi * q.lg * g;
+      const double qg_p = w.wi * fma(q.lg_p, g, -q.lg);
+      const double qg_x = w.wi * q.lg_x * g;
+      src[2] = fma(q.rs, src[1], qg);
+      d[2][0] = fma(q.rs, d[1][0], fma(q.rs_p, src[1], qg_p));
+      d[2][1] = q.rs * d[1][1];
+      d[2][2] = fma(q.rs, d[1][2], fma(q.rs_x, src[1], qg_x));
+    }
+  } else {
+    const double drive = w.p_bh - q.p;
+    if (!positive(drive)) return;
+    const int e = (w.phase == 0) ? 0 : NB - 1;
+    const double b = (w.phase == 0) ? a.bw : a.bg;
+    const double b_p = (w.phase == 0) ? a.bw_p : a.bg_p;
+    const double wmb = w.wi * a.mob * b;
+    src[e] = wmb * drive;
+    d[e][0] = w.wi * fma(fma(a.mob_p, b, a.mob * b_p), drive, -a.mob * b);
+    d[e][1] = w.wi * a.mob_sw * b * drive;
+    d[e][2] = w.wi * a.mob_x * b * drive;
+  }
+}
+
+}  // namespace ocp

@@ -1,0 +1,328 @@
+// Block-CSR products and the adjoint vector-Jacobian product.
+//
+// spmv_kernel       y = alpha A x + beta y on the grid's 7-point block pattern
+//                   (the kernel the linear solver iterates on, Sec. 3.3.3);
+// spmv_t_kernel     the transposed product, gathered through the mirror map
+//                   (block (c, n) <-> block (n, c)) so that every output row is
+//                   owned by one thread and no atomics are needed;
+// vjp_kernel        lambda^T dR/d(u_new, u_old, ln k, phi) of the residual of
+//                   eqs. 1, 2 and 4: J^T lambda through the mirror map, the
+//                   transmissibility and well-index terms from the stored face
+//                   fluxes (T and WI are linear in the fluxes), and the
+//                   accumulation terms recomputed from the two states.
+// setup_kernel      per-grid geometry: transmissibilities, their ln k weights,
+//                   the block-CSR pattern and the mirror map.
+// well_rate_kernel  surface rates of each well (one thread per well, its
+//                   perforations summed in order).
+#include "ocp_internal.cuh"
+#include "kernels.cuh"
+
+namespace ocp {
+
+namespace {
+
+// ------------------------------------------------------------------ pattern
+// Neighbour types in column order: -z, -y, -x, self, +x, +y, +z.
+__device__ __forceinline__ void neighbours(const Params& P, long long c, bool* has) {
+  const int i = (int)(c % P.nx);
+  const int j = (int)((c / P.nx) % P.ny);
+  const int k = (int)(c / P.nxy);
+  has[0] = k > 0; has[1] = j > 0; has[2] = i > 0; has[3] = true;
+  has[4] = i + 1 < P.nx; has[5] = j + 1 < P.ny; has[6] = k + 1 < P.nz;
+}
+
+// Number of stored blocks in the rows before c (closed form of the prefix
+// sum of 7 minus the missing neighbours of every earlier cell).
+__device__ __forceinline__ long long row_start(const Params& P, long long c) {
+  const long long nx = P.nx, nxy = P.nxy, N = P.N;
+  const long long i0 = (c + nx - 1) / nx;                 // earlier cells with i == 0
+  const long long iL = c / nx;                            // ... with i == nx-1
+  const long long lay = c / nxy, rem = c % nxy;
+  const long long j0 = lay * nx + (rem < nx ? rem : nx);  // ... with j == 0
+  const long long jL = lay * nx + (rem > nxy - nx ? rem - (nxy - nx) : 0);
+  const long long k0 = c < nxy ? c : nxy;                 // ... with k == 0
+  const long long kL = c > N - nxy ? c - (N - nxy) : 0;   // ... with k == nz-1
+  return 7 * c - (i0 + iL + j0 + jL + k0 + kL);
+}
+
+__global__ void setup_kernel(Params P, const double* __restrict__ lnk, double dx, double dy, double dz,
+                             double kzr, double* __restrict__ trans, double* __restrict__ wlnk,
+                             int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
+                             int32_t* __restrict__ mirror) {
+  const long long N = P.N;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const long long off[7] = {-P.nxy, -P.nx, -1, 0, 1, P.nx, P.nxy};
+  bool has[7];
+  neighbours(P, c, has);
+  // transmissibility of the +x, +y, +z face: harmonic combination of the two
+  // half-cell conductances C A / (h/(2 k_c) + h/(2 k_n))
+  const double h[3] = {dx, dy, dz};
+  const double area[3] = {dy * dz, dx * dz, dx * dy};
+  const double kc = exp(lnk[c]);
+  for (int d = 0; d < 3; ++d) {
+    double T = 0.0, wi = 0.0, wj = 0.0;
+    if (has[4 + d]) {
+      const double kn = exp(lnk[c + off[4 + d]]);
+      const double fz = (d == 2) ? kzr : 1.0;
+      const double ki_ = kc * fz, kj_ = kn * fz;
+      T = (kDarcy * area[d]) / ((0.5 * h[d]) / ki_ + (0.5 * h[d]) / kj_);
+      wi = kn / (kc + kn);   // d ln T / d ln k_c
+      wj = kc / (kc + kn);   // d ln T / d ln k_n
+    }
+    trans[d * N + c] = T;
+    wlnk[d * N + c] = wi;
+    wlnk[(3 + d) * N + c] = wj;
+  }
+  const long long start = row_start(P, c);
+  row_ptr[c] = (int32_t)start;
+  if (c == N - 1) row_ptr[N] = (int32_t)row_start(P, N);
+  int s = 0;
+  for (int t = 0; t < 7; ++t) {
+    if (!has[t]) continue;
+    const long long n = c + off[t];
+    col_idx[start + s] = (int32_t)n;
+    // slot of the opposite type (6 - t) in row n
+    bool hn[7];
+    neighbours(P, n, hn);
+    int sn = 0;
+    for (int u = 0; u < 6 - t; ++u) sn += hn[u];
+    mirror[start + s] = (int32_t)(row_start(P, n) + sn);
+    ++s;
+  }
+}
+
+// ------------------------------------------------------------------ SpMV
+// mode 0: y = A x;  1: y = alpha A x;  2: y = alpha A x + beta y
+template <int NB, bool TRANS>
+__global__ void __launch_bounds__(256) spmv_kernel(long long N, const int32_t* __restrict__ row_ptr,
+                                                   const int32_t* __restrict__ col_idx,
+                                                   const int32_t* __restrict__ mirror,
+                                                   const double* __restrict__ val, double alpha,
+                                                   const double* __restrict__ x, double beta,
+                                                   double* __restrict__ y, int mode) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  double acc[NB];
+#pragma unroll
+  for (int e = 0; e < NB; ++e) acc[e] = 0.0;
+  const int s0 = row_ptr[c], s1 = row_ptr[c + 1];
+  for (int s = s0; s < s1; ++s) {
+    const long long n = col_idx[s];
+    const double* blk = val + (long long)(TRANS ? mirror[s] : s) * NB * NB;
+    double xv[NB];
+#pragma unroll
+    for (int v = 0; v < NB; ++v) xv[v] = x[n * NB + v];
+#pragma unroll
+    for (int e = 0; e < NB; ++e)
+#pragma unroll
+      for (int v = 0; v < NB; ++v) {
+        if (TRANS) acc[e] = fma(blk[v * NB + e], xv[v], acc[e]);
+        else acc[e] = fma(blk[e * NB + v], xv[v], acc[e]);
+      }
+  }
+#pragma unroll
+  for (int e = 0; e < NB; ++e) {
+    double o = acc[e];
+    if (mode >= 1) o = alpha * o;
+    if (mode == 2) o = fma(beta, y[c * NB + e], o);
+    y[c * NB + e] = o;
+  }
+}
+
+// ------------------------------------------------------------------ adjoint
+template <int NB>
+__global__ void __launch_bounds__(256) vjp_kernel(Params P, const Table* __restrict__ gT,
+                                                  const double* __restrict__ u_new,
+                                                  const int8_t* __restrict__ f_new,
+                                                  const double* __restrict__ u_old,
+                                                  const int8_t* __restrict__ f_old,
+                                                  const double* __restrict__ phi,
+                                                  const int32_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col_idx,
+                                                  const int32_t* __restrict__ mirror,
+                                                  const double* __restrict__ val,
+                                                  const double* __restrict__ face_flux,
+                                                  const double* __restrict__ wlnk,
+                                                  const int32_t* __restrict__ perf_of_cell,
+                                                  const Perf* __restrict__ perf, double scale,
+                                                  const double* __restrict__ lam,
+                                                  double* __restrict__ g_unew, double* __restrict__ g_uold,
+                                                  double* __restrict__ g_lnk, double* __restrict__ g_phi) {
+  __shared__ Table T;
+  for (int i = threadIdx.x; i < (int)(sizeof(Table) / 8); i += blockDim.x)
+    reinterpret_cast<double*>(&T)[i] = reinterpret_cast<const double*>(gT)[i];
+  __syncthreads();
+  const long long N = P.N;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  double lc[NB];
+#pragma unroll
+  for (int e = 0; e < NB; ++e) lc[e] = lam[c * NB + e];
+
+  if (g_unew) {
+    double acc[NB];
+#pragma unroll
+    for (int v = 0; v < NB; ++v) acc[v] = 0.0;
+    for (int s = row_ptr[c]; s < row_ptr[c + 1]; ++s) {
+      const long long n = col_idx[s];
+      const double* blk = val + (long long)mirror[s] * NB * NB;
+#pragma unroll
+      for (int e = 0; e < NB; ++e) {
+        const double l = lam[n * NB + e];
+#pragma unroll
+        for (int v = 0; v < NB; ++v) acc[v] = fma(blk[e * NB + v], l, acc[v]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NB; ++v) g_unew[v * N + c] = acc[v];
+  }
+
+  const double pn = u_new[c], swn = u_new[N + c], xn = (NB == 3) ? u_new[2 * N + c] : 0.0;
+  const double po = u_old[c], swo = u_old[N + c], xo = (NB == 3) ? u_old[2 * N + c] : 0.0;
+  const int fn = (NB == 3) ? (f_new[c] & 1) : 0, fo = (NB == 3) ? (f_old[c] & 1) : 0;
+  const double ph = phi[c];
+
+  if (g_uold || g_phi) {
+    CellQ q{};
+    CellAux ao{};
+    cell_quantities<NB, true>(P, T, po, swo, xo, fo, ph, q, ao);
+    if (g_uold) {
+      double g[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int e = 0; e < NB; ++e) {
+        g[0] = fma(lc[e], ao.m_p[e], g[0]);
+        g[1] = fma(lc[e], ao.m_sw[e], g[1]);
+        g[2] = fma(lc[e], ao.m_x[e], g[2]);
+      }
+#pragma unroll
+      for (int v = 0; v < NB; ++v) g_uold[v * N + c] = -scale * g[v];
+    }
+    if (g_phi) {
+      // the accumulation is linear in the reference porosity
+      double mn[3], mo[3];
+      cell_masses<NB>(P, T, pn, swn, xn, fn, 1.0, mn);
+      cell_masses<NB>(P, T, po, swo, xo, fo, 1.0, mo);
+      double g = 0.0;
+#pragma unroll
+      for (int e = 0; e < NB; ++e) g = fma(lc[e], mn[e] - mo[e], g);
+      g_phi[c] = scale * g;
+    }
+  }
+
+  if (g_lnk) {
+    bool has[7];
+    neighbours(P, c, has);
+    const long long stride[3] = {1, P.nx, P.nxy};
+    double g = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      if (has[4 + d]) {              // + face: this cell is the upstream index i
+        const long long n = c + stride[d];
+        const double w = wlnk[d * N + c];
+        double t = 0.0;
+#pragma unroll
+        for (int e = 0; e < NB; ++e) t = fma(lc[e] - lam[n * NB + e], face_flux[(d * NB + e) * N + c], t);
+        g = fma(w, t, g);
+      }
+      if (has[2 - d]) {              // - face: this cell is j of the face (n, c)
+        const long long n = c - stride[d];
+        const double w = wlnk[(3 + d) * N + n];
+        double t = 0.0;
+#pragma unroll
+        for (int e = 0; e < NB; ++e) t = fma(lam[n * NB + e] - lc[e], face_flux[(d * NB + e) * N + n], t);
+        g = fma(w, t, g);
+      }
+    }
+    const int ip = perf_of_cell[c];
+    if (ip >= 0) {                   // the well index is proportional to k of the cell
+      CellQ q{};
+      CellAux a{};
+      cell_quantities<NB, true>(P, T, pn, swn, xn, fn, ph, q, a);
+      double src[3], ds[3][3];
+      well_source<NB>(perf[ip], q, a, src, ds);
+#pragma unroll
+      for (int e = 0; e < NB; ++e) g = fma(-lc[e], src[e], g);
+    }
+    g_lnk[c] = g;
+  }
+}
+
+// ------------------------------------------------------------------ wells
+template <int NB>
+__global__ void well_rate_kernel(Params P, const Table* __restrict__ gT, const double* __restrict__ u,
+                                 const int8_t* __restrict__ flag, const double* __restrict__ phi,
+                                 const Perf* __restrict__ perf, const int32_t* __restrict__ first,
+                                 int nwell, double* __restrict__ q) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwell) return;
+  const long long N = P.N;
+  double sum[3] = {0.0, 0.0, 0.0};
+  for (int k = first[w]; k < first[w + 1]; ++k) {
+    const long long c = perf[k].cell;
+    CellQ cq{};
+    CellAux a{};
+    cell_quantities<NB, true>(P, *gT, u[c], u[N + c], (NB == 3) ? u[2 * N + c] : 0.0,
+                              (NB == 3) ? (flag[c] & 1) : 0, phi[c], cq, a);
+    double src[3], ds[3][3];
+    well_source<NB>(perf[k], cq, a, src, ds);
+    for (int e = 0; e < NB; ++e) sum[e] += src[e];
+  }
+  for (int e = 0; e < NB; ++e) q[w * NB + e] = sum[e];
+}
+
+}  // namespace
+
+cudaError_t launch_setup(ocp_grid* g, const double* d_lnk, double dx, double dy, double dz,
+                         double kz_over_kx, cudaStream_t s) {
+  const Params& P = g->prm;
+  const unsigned blocks = (unsigned)((P.N + 255) / 256);
+  setup_kernel<<<blocks, 256, 0, s>>>(P, d_lnk, dx, dy, dz, kz_over_kx, g->d_trans, g->d_wlnk,
+                                      g->d_row_ptr, g->d_col_idx, g->d_mirror);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, const double* x, double beta,
+                        double* y, int transpose, cudaStream_t s) {
+  const long long N = g->prm.N;
+  const unsigned blocks = (unsigned)((N + 255) / 256);
+  const int mode = (beta != 0.0) ? 2 : (alpha != 1.0 ? 1 : 0);
+  if (g->prm.nb == 3) {
+    if (transpose) spmv_kernel<3, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+    else spmv_kernel<3, false><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+  } else {
+    if (transpose) spmv_kernel<2, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+    else spmv_kernel<2, false><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vjp(const ocp_grid* g, const double* u_new, const int8_t* f_new, const double* u_old,
+                       const int8_t* f_old, double dt, const double* val, const double* face_flux,
+                       const double* lam, double* g_unew, double* g_uold, double* g_lnk, double* g_phi,
+                       cudaStream_t s) {
+  const Params& P = g->prm;
+  const unsigned blocks = (unsigned)((P.N + 255) / 256);
+  const double scale = P.vol_rb / dt;
+  if (P.nb == 3)
+    vjp_kernel<3><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, g->d_row_ptr,
+                                         g->d_col_idx, g->d_mirror, val, face_flux, g->d_wlnk, g->d_perf_of_cell,
+                                         g->d_perf, scale, lam, g_unew, g_uold, g_lnk, g_phi);
+  else
+    vjp_kernel<2><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, g->d_row_ptr,
+                                         g->d_col_idx, g->d_mirror, val, face_flux, g->d_wlnk, g->d_perf_of_cell,
+                                         g->d_perf, scale, lam, g_unew, g_uold, g_lnk, g_phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_well_rates(const ocp_grid* g, const double* u, const int8_t* flag, double* q,
+                              cudaStream_t s) {
+  if (g->nwell == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((g->nwell + 63) / 64);
+  if (g->prm.nb == 3)
+    well_rate_kernel<3><<<blocks, 64, 0, s>>>(g->prm, g->d_table, u, flag, g->d_phi, g->d_perf, g->d_well_first, g->nwell, q);
+  else
+    well_rate_kernel<2><<<blocks, 64, 0, s>>>(g->prm, g->d_table, u, flag, g->d_phi, g->d_perf, g->d_well_first, g->nwell, q);
+  return cudaGetLastError();
+}
+
+}  // namespace ocp

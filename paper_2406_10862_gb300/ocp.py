@@ -1,0 +1,288 @@
+"""Thin Python binding of the C interface in ``include/ocp.h``.
+
+Only argument marshalling happens here: every computation runs in the CUDA
+kernels of ``_build/libocp.so``.  There is no fallback -- if the library has
+not been built, or no CUDA device is present, using it raises.  Device memory
+and streams come from PyTorch: arrays are ``torch.Tensor`` objects on the
+grid's device, and calls are enqueued on the current PyTorch stream of that
+device unless a stream is given.
+
+The functions keep the C names (``ocp_linearize`` ...); ``Grid`` wraps them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OCP_OK, OCP_ERR_INVALID_ARG, OCP_ERR_CUDA, OCP_ERR_OOM = 0, 1, 2, 3
+OCP_ERR_NONFINITE, OCP_ERR_TIMEOUT, OCP_ERR_UNSUPPORTED = 4, 5, 6
+STATUS_NAMES = {0: "OCP_OK", 1: "OCP_ERR_INVALID_ARG", 2: "OCP_ERR_CUDA", 3: "OCP_ERR_OOM",
+                4: "OCP_ERR_NONFINITE", 5: "OCP_ERR_TIMEOUT", 6: "OCP_ERR_UNSUPPORTED"}
+
+# Every symbol the header declares; the CPU tests check the library exports them.
+EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_pattern", "ocp_linearize",
+           "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
+
+
+class OcpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class _Well(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("phase", ctypes.c_int), ("p_bh", ctypes.c_double),
+                ("rw", ctypes.c_double), ("skin", ctypes.c_double), ("nperf", ctypes.c_int),
+                ("cells", ctypes.POINTER(ctypes.c_int64))]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("top_depth", ctypes.c_double), ("nphase", ctypes.c_int),
+                ("lnk", _D), ("phi", _D),
+                ("kz_over_kx", ctypes.c_double), ("cr", ctypes.c_double), ("p_ref", ctypes.c_double),
+                ("nrow", ctypes.c_int),
+                ("tab_p", _D), ("tab_Bo", _D), ("tab_Bg", _D), ("tab_Rs", _D), ("tab_muo", _D), ("tab_mug", _D)]
+    _fields_ += [(n, ctypes.c_double) for n in
+                 ("bw_ref", "cw", "muw", "rho_osc", "rho_gsc", "rho_wsc", "co_under", "cmu_under",
+                  "swc", "sorw", "sorg", "sgc", "nw", "now", "ng", "nog", "krw_max", "krg_max", "kro_cw",
+                  "pcow_max", "pcgo_max")]
+    _fields_ += [("nwell", ctypes.c_int), ("wells", ctypes.POINTER(_Well))]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libocp.so (building it first only when asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libocp.so is not built (%s); run __graft_entry__.build()" % path)
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i64, i32p = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)
+    lib.ocp_grid_create.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.POINTER(vp)]
+    lib.ocp_grid_destroy.argtypes = [vp]
+    lib.ocp_grid_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64)]
+    lib.ocp_bsr_pattern.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.ocp_linearize.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp]
+    lib.ocp_bsr_spmv.argtypes = [vp, vp, ctypes.c_double, vp, ctypes.c_double, vp, ctypes.c_int, vp]
+    lib.ocp_adjoint_vjp.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.ocp_well_rates.argtypes = [vp, vp, vp, vp, vp]
+    lib.ocp_get_status.argtypes = [vp, vp]
+    lib.ocp_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "ocp_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != OCP_OK:
+        raise OcpError(st, _lib.ocp_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(device, stream):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class _DevView:
+    """Zero-copy view of device memory owned by the library."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3}
+
+
+def make_desc(desc):
+    """The C descriptor of a ``workloads.GridDesc``-like object, and the host
+    arrays it points into (keep them alive while the descriptor is used)."""
+    keep = []
+
+    def arr(a, dtype=np.float64):
+        a = np.ascontiguousarray(a, dtype=dtype)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double if dtype == np.float64 else ctypes.c_int64))
+
+    d = _Desc()
+    for name in ("nx", "ny", "nz", "nphase"):
+        setattr(d, name, int(getattr(desc, name)))
+    for name in ("dx", "dy", "dz", "top_depth", "kz_over_kx", "cr", "p_ref", "bw_ref", "cw", "muw",
+                 "rho_osc", "rho_gsc", "rho_wsc", "co_under", "cmu_under", "swc", "sorw", "sorg", "sgc",
+                 "nw", "now", "ng", "nog", "krw_max", "krg_max", "kro_cw", "pcow_max", "pcgo_max"):
+        setattr(d, name, float(getattr(desc, name)))
+    d.lnk = arr(desc.lnk)
+    d.phi = arr(desc.phi)
+    d.nrow = len(desc.tab_p)
+    for name in ("tab_p", "tab_Bo", "tab_Bg", "tab_Rs", "tab_muo", "tab_mug"):
+        setattr(d, name, arr(getattr(desc, name)))
+    wells = (_Well * max(1, len(desc.wells)))()
+    keep.append(wells)
+    for k, w in enumerate(desc.wells):
+        wells[k].kind = int(w.kind)
+        wells[k].phase = int(w.phase)
+        wells[k].p_bh = float(w.p_bh)
+        wells[k].rw = float(w.rw)
+        wells[k].skin = float(w.skin)
+        wells[k].nperf = len(w.cells)
+        wells[k].cells = arr(w.cells, np.int64)
+    d.nwell = len(desc.wells)
+    d.wells = wells
+    return d, keep
+
+
+class Grid:
+    """A grid on one CUDA device (``ocp_grid_create``); owns its device data."""
+
+    def __init__(self, desc, device=0):
+        lib = load()
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        d, keep = make_desc(desc)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.ocp_grid_create(ctypes.byref(d), self.device.index or 0, ctypes.byref(h)))
+        self._h = h
+        del keep
+        n, nb, nnzb = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+        _check(lib.ocp_grid_info(h, ctypes.byref(n), ctypes.byref(nb), ctypes.byref(nnzb)))
+        self.N, self.nb, self.nnzb = n.value, nb.value, nnzb.value
+        self.nwell = len(desc.wells)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ocp_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ helpers
+    def _t(self, t, numel, dtype, name, allow_none=False):
+        if t is None:
+            if allow_none:
+                return None
+            raise ValueError("%s is required" % name)
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != dtype:
+            raise ValueError("%s must be a %s tensor on %s" % (name, dtype, self.device))
+        if not t.is_contiguous() or t.numel() != numel:
+            raise ValueError("%s must be contiguous with %d elements (got %d)" % (name, numel, t.numel()))
+        return t
+
+    def empty(self, n, dtype=torch.float64):
+        return torch.empty(n, dtype=dtype, device=self.device)
+
+    def pattern(self):
+        """(row_ptr, col_idx): int32 device tensors holding copies of the grid's pattern."""
+        rp, ci = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load().ocp_bsr_pattern(self._h, ctypes.byref(rp), ctypes.byref(ci)))
+        row_ptr = torch.as_tensor(_DevView(rp.value, self.N + 1, "<i4"), device=self.device).clone()
+        col_idx = torch.as_tensor(_DevView(ci.value, self.nnzb, "<i4"), device=self.device).clone()
+        return row_ptr, col_idx
+
+    # ------------------------------------------------------------ calls
+    def linearize(self, u_new, flag_new, u_old, flag_old, dt, residual=None, bsr_val=None,
+                  face_flux=None, want_face_flux=False, stream=None):
+        N, nb = self.N, self.nb
+        self._t(u_new, nb * N, torch.float64, "u_new")
+        self._t(u_old, nb * N, torch.float64, "u_old")
+        if nb == 3 or flag_new is not None:
+            self._t(flag_new, N, torch.int8, "flag_new")
+            self._t(flag_old, N, torch.int8, "flag_old")
+        residual = residual if residual is not None else self.empty(nb * N)
+        bsr_val = bsr_val if bsr_val is not None else self.empty(self.nnzb * nb * nb)
+        if face_flux is None and want_face_flux:
+            face_flux = self.empty(3 * nb * N)
+        self._t(residual, nb * N, torch.float64, "residual")
+        self._t(bsr_val, self.nnzb * nb * nb, torch.float64, "bsr_val")
+        self._t(face_flux, 3 * nb * N, torch.float64, "face_flux", allow_none=True)
+        _check(load().ocp_linearize(self._h, _ptr(u_new), _ptr(flag_new), _ptr(u_old), _ptr(flag_old),
+                                    float(dt), _ptr(residual), _ptr(bsr_val), _ptr(face_flux),
+                                    _stream(self.device, stream)))
+        return residual, bsr_val, face_flux
+
+    def spmv(self, bsr_val, x, alpha=1.0, beta=0.0, y=None, transpose=False, stream=None):
+        n = self.nb * self.N
+        self._t(bsr_val, self.nnzb * self.nb * self.nb, torch.float64, "bsr_val")
+        self._t(x, n, torch.float64, "x")
+        y = y if y is not None else self.empty(n)
+        self._t(y, n, torch.float64, "y")
+        _check(load().ocp_bsr_spmv(self._h, _ptr(bsr_val), float(alpha), _ptr(x), float(beta), _ptr(y),
+                                   int(bool(transpose)), _stream(self.device, stream)))
+        return y
+
+    def adjoint_vjp(self, u_new, flag_new, u_old, flag_old, dt, bsr_val, face_flux, lam,
+                    want=("unew", "uold", "lnk", "phi"), out=None, stream=None):
+        N, nb = self.N, self.nb
+        self._t(lam, nb * N, torch.float64, "lambda")
+        out = dict(out or {})
+        sizes = {"unew": nb * N, "uold": nb * N, "lnk": N, "phi": N}
+        for k in want:
+            if k not in out:
+                out[k] = self.empty(sizes[k])
+            self._t(out[k], sizes[k], torch.float64, "g_" + k)
+        _check(load().ocp_adjoint_vjp(self._h, _ptr(u_new), _ptr(flag_new), _ptr(u_old), _ptr(flag_old),
+                                      float(dt), _ptr(bsr_val), _ptr(face_flux), _ptr(lam),
+                                      _ptr(out.get("unew")), _ptr(out.get("uold")), _ptr(out.get("lnk")),
+                                      _ptr(out.get("phi")), _stream(self.device, stream)))
+        return out
+
+    def well_rates(self, u, flag, q=None, stream=None):
+        q = q if q is not None else self.empty(max(1, self.nwell) * self.nb)
+        _check(load().ocp_well_rates(self._h, _ptr(u), _ptr(flag), _ptr(q), _stream(self.device, stream)))
+        return q[: self.nwell * self.nb]
+
+    def status(self, stream=None):
+        """Synchronise and return the sticky device status (an int, 0 = OK)."""
+        return load().ocp_get_status(self._h, _stream(self.device, stream))
+
+
+# C names, for callers who prefer the flat interface
+def ocp_grid_create(desc, device=0):
+    return Grid(desc, device)
+
+
+def ocp_linearize(grid, *a, **k):
+    return grid.linearize(*a, **k)
+
+
+def ocp_bsr_spmv(grid, *a, **k):
+    return grid.spmv(*a, **k)
+
+
+def ocp_adjoint_vjp(grid, *a, **k):
+    return grid.adjoint_vjp(*a, **k)
+
+
+def ocp_well_rates(grid, *a, **k):
+    return grid.well_rates(*a, **k)
+
+
+def ocp_get_status(grid, stream=None):
+    return grid.status(stream)

@@ -1,0 +1,51 @@
+"""Shared helpers of the GPU parity tests: moving seeded inputs to the device,
+running the library and the oracle on the same inputs, and the tolerances.
+
+Tolerances (FP64, differing summation order): every residual entry within
+1e-12 and every Jacobian entry within 1e-10 of the oracle, relative to the
+entry's magnitude scale -- the sum of the absolute values of the terms that
+form it, carried through the oracle's dual numbers (``oracle.dual``).  The
+scale is what bounds rounding differences between two evaluation orders of
+the same sums; the plain relative error is meaningless where terms cancel.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+RTOL_R = 1e-12
+RTOL_J = 1e-10
+RTOL_SPMV = 1e-13
+RTOL_VJP = 1e-10
+
+
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def dev_state(s, device="cuda"):
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=device)
+    return (f(s.u_new.ravel()), f(s.flag_new.astype(np.int8)), f(s.u_old.ravel()),
+            f(s.flag_old.astype(np.int8)))
+
+
+def gpu_linearize(grid, s, want_face_flux=True):
+    un, fn, uo, fo = dev_state(s)
+    r, v, ff = grid.linearize(un, fn, uo, fo, s.dt, want_face_flux=want_face_flux)
+    st = grid.status()
+    return r.cpu().numpy(), v.cpu().numpy(), (ff.cpu().numpy() if ff is not None else None), st
+
+
+def assert_scaled_close(got, ref, mag, rtol, what):
+    got = np.asarray(got).ravel()
+    ref = np.asarray(ref).ravel()
+    mag = np.asarray(mag).ravel()
+    err = np.abs(got - ref)
+    lim = rtol * mag + 1e-300
+    bad = np.nonzero(err > lim)[0]
+    if len(bad):
+        k = bad[np.argmax(err[bad] / lim[bad])]
+        raise AssertionError("%s: %d of %d entries off; worst index %d got %.17g ref %.17g scale %.3g "
+                             "(err/scale %.3g)" % (what, len(bad), len(err), k, got[k], ref[k], mag[k],
+                                                    err[k] / max(mag[k], 1e-300)))
