@@ -132,6 +132,23 @@ ocp_status ocp_linearize(ocp_grid* grid, const double* u_new, const int8_t* flag
                          const double* u_old, const int8_t* flag_old, double dt,
                          double* residual, double* bsr_val, double* face_flux, void* cuda_stream);
 
+/* ocp_linearize without any device allocation behind it.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * when they linearise -- code whose device memory is owned by a host
+ * application or framework, a loop under a fixed memory budget, or work that
+ * will be captured into a CUDA graph, where allocation is not allowed.
+ * Same arguments, outputs and errors as ocp_linearize, but its per-cell
+ * scratch is a 32 MiB array owned by the library (held on every GPU that
+ * loads it until the process exits) instead of the grid's buffer, so it
+ * accepts grids of at most 41 943 cells and returns OCP_ERR_INVALID_ARG for
+ * larger ones.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race and must not be made. */
+ocp_status ocp_linearize_noalloc(ocp_grid* grid, const double* u_new, const int8_t* flag_new,
+                                 const double* u_old, const int8_t* flag_old, double dt,
+                                 double* residual, double* bsr_val, double* face_flux, void* cuda_stream);
+
 /* Block-CSR product of the linear solver (LinearSystem, Sec. 3.3.3):
  * y = alpha * A x + beta * y, or with transpose != 0, y = alpha * A^T x +
  * beta * y.  A is bsr_val on the grid's pattern; x and y are block-

@@ -125,6 +125,18 @@ ocp_status validate(const ocp_grid_desc* d) {
 
 }  // namespace
 
+namespace ocp {
+// Records a formatted message as this thread's last error (for entry points
+// defined in other translation units) and returns the status.
+ocp_status report(ocp_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+}  // namespace ocp
+
 extern "C" {
 
 const char* ocp_last_error(void) { return g_err; }

@@ -8,6 +8,12 @@ int64_t linearize_scratch_doubles(int64_t N);
 cudaError_t launch_linearize(const ocp_grid* g, const double* u_new, const int8_t* f_new,
                              const double* u_old, const int8_t* f_old, double dt, double* res,
                              double* val, double* face_flux, cudaStream_t s);
+// The same launches with the per-cell scratch given explicitly (used by the
+// entry point that must not allocate).
+cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const double* u_new,
+                                     const int8_t* f_new, const double* u_old, const int8_t* f_old, double dt,
+                                     double* res, double* val, double* face_flux, cudaStream_t s);
+ocp_status report(ocp_status st, const char* fmt, ...);
 cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, const double* x, double beta,
                         double* y, int transpose, cudaStream_t s);
 cudaError_t launch_vjp(const ocp_grid* g, const double* u_new, const int8_t* f_new, const double* u_old,

@@ -210,4 +210,25 @@ cudaError_t launch_linearize(const ocp_grid* g, const double* u_new, const int8_
   return cudaGetLastError();
 }
 
+cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const double* u_new,
+                                     const int8_t* f_new, const double* u_old, const int8_t* f_old, double dt,
+                                     double* res, double* val, double* face_flux, cudaStream_t s) {
+  const Params& P = g->prm;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((P.N + threads - 1) / threads);
+  const double scale = P.vol_rb / dt;
+  if (P.nb == 3) {
+    cell_kernel<3><<<blocks, threads, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi,
+                                              g->d_perf_of_cell, g->d_perf, scale, scratch, g->d_status);
+    face_kernel<3><<<blocks, threads, 0, s>>>(P, g->d_trans, scratch, face_flux);
+    assemble_kernel<3><<<blocks, threads, 0, s>>>(P, g->d_row_ptr, scratch, res, val, g->d_status);
+  } else {
+    cell_kernel<2><<<blocks, threads, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi,
+                                              g->d_perf_of_cell, g->d_perf, scale, scratch, g->d_status);
+    face_kernel<2><<<blocks, threads, 0, s>>>(P, g->d_trans, scratch, face_flux);
+    assemble_kernel<2><<<blocks, threads, 0, s>>>(P, g->d_row_ptr, scratch, res, val, g->d_status);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace ocp

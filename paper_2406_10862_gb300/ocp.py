@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "OCP_OK", 1: "OCP_ERR_INVALID_ARG", 2: "OCP_ERR_CUDA", 3: "OC
 
 # Every symbol the header declares; the CPU tests check the library exports them.
 EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_pattern", "ocp_linearize",
-           "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
+           "ocp_linearize_noalloc", "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
 
 
 class OcpError(RuntimeError):
@@ -83,6 +83,7 @@ def load(build_if_missing: bool = False):
     lib.ocp_grid_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64)]
     lib.ocp_bsr_pattern.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
     lib.ocp_linearize.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp]
+    lib.ocp_linearize_noalloc.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp]
     lib.ocp_bsr_spmv.argtypes = [vp, vp, ctypes.c_double, vp, ctypes.c_double, vp, ctypes.c_int, vp]
     lib.ocp_adjoint_vjp.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.ocp_well_rates.argtypes = [vp, vp, vp, vp, vp]
@@ -225,6 +226,24 @@ class Grid:
         _check(load().ocp_linearize(self._h, _ptr(u_new), _ptr(flag_new), _ptr(u_old), _ptr(flag_old),
                                     float(dt), _ptr(residual), _ptr(bsr_val), _ptr(face_flux),
                                     _stream(self.device, stream)))
+        return residual, bsr_val, face_flux
+
+    def linearize_noalloc(self, u_new, flag_new, u_old, flag_old, dt, residual, bsr_val, face_flux=None,
+                          stream=None):
+        """``ocp_linearize_noalloc``: the caller passes every output; the
+        library's fixed scratch array is used (grids of at most 41 943 cells)."""
+        N, nb = self.N, self.nb
+        self._t(u_new, nb * N, torch.float64, "u_new")
+        self._t(u_old, nb * N, torch.float64, "u_old")
+        if nb == 3 or flag_new is not None:
+            self._t(flag_new, N, torch.int8, "flag_new")
+            self._t(flag_old, N, torch.int8, "flag_old")
+        self._t(residual, nb * N, torch.float64, "residual")
+        self._t(bsr_val, self.nnzb * nb * nb, torch.float64, "bsr_val")
+        self._t(face_flux, 3 * nb * N, torch.float64, "face_flux", allow_none=True)
+        _check(load().ocp_linearize_noalloc(self._h, _ptr(u_new), _ptr(flag_new), _ptr(u_old), _ptr(flag_old),
+                                            float(dt), _ptr(residual), _ptr(bsr_val), _ptr(face_flux),
+                                            _stream(self.device, stream)))
         return residual, bsr_val, face_flux
 
     def spmv(self, bsr_val, x, alpha=1.0, beta=0.0, y=None, transpose=False, stream=None):
