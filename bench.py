@@ -352,7 +352,7 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": "flushed before every step (512 MB write outside the step events)"},
             "phases_ms": {"linearize": statistics.mean(lin), "spmv_each": spmv_ms, "vjp": statistics.mean(vjp),
                           "wall_timed_region_ms": wall * 1e3},
-            "roofline": {"kernel": "spmv_kernel<3,false>", "bound": "alu", "achieved": achieved,
+            "roofline": {"kernel": "spmv_grid_kernel<3>", "bound": "alu", "achieved": achieved,
                          "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
                          "peak_source": "measured FP64 FMA rate (profiles/fp64_peak_probe.md)",
                          "traffic": None,

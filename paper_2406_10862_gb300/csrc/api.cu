@@ -222,6 +222,11 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   P.krw_max = d->krw_max; P.krg_max = d->krg_max; P.kc = d->kro_cw;
   P.pcow_max = d->pcow_max; P.pcgo_max = (nb == 3) ? d->pcgo_max : 0.0;
   P.grav_dz = 0.5 * ocp::kGrav * d->dz;
+  P.pcow2 = 2.0 * d->pcow_max;
+  P.pcgo2 = (nb == 3) ? 2.0 * d->pcgo_max : 0.0;
+  P.bw_p = d->bw_ref * d->cw;
+  P.rw_p = (d->bw_ref * d->cw) * d->rho_wsc;
+  P.bw_p_imu = (d->bw_ref * d->cw) * P.imu_w;
   P.vol_rb = d->dx * d->dy * d->dz / ocp::kRbFt3;
 
   g->nnzb = 7 * N - 2 * ((long long)d->ny * d->nz + (long long)d->nx * d->nz + (long long)d->nx * d->ny);

@@ -55,6 +55,9 @@ struct Params {
   double pcow_max, pcgo_max;
   double grav_dz;                         // 0.5 * g * dz: half the potential head per unit density
   double vol_rb;                          // cell bulk volume in rb
+  double pcow2, pcgo2;                    // 2 Pc_max (derivative factors)
+  double bw_p;                            // d b_w / dp
+  double rw_p, bw_p_imu;                  // d rho_w / dp, (d b_w / dp) / mu_w
 };
 
 // Well perforation data on the device (one entry per perforated cell).
@@ -160,21 +163,26 @@ struct CellAux {
   double bw, bw_p, bg, bg_p;                // injected-phase b and its p-derivative
 };
 
-// PVT, rock, Corey / Stone II, capillary pressure, densities and mobilities
-// of one cell (Bulk: PVT, SAT, ROCK modules, Sec. 3.2.3).
-template <int NB, bool AUX>
-__device__ __forceinline__ void cell_quantities(const Params& P, const Table& T, double p, double sw,
-                                                double x, int flag, double phi_ref, CellQ& q,
-                                                CellAux& a) {
+// Fluid (PVT module) quantities of one cell with their derivatives with
+// respect to (p, X); saturated cells read the tables at p, undersaturated
+// cells at the bubble point of their R_s (Sec. 3.2.3, PVT).  VISC also
+// evaluates the reciprocal viscosities.
+struct Pvt {
+  double bw, bw_p;
+  double bo, bo_p, bo_x, imo, imo_p, imo_x;
+  double rs, rs_p, rs_x, sg, sg_x;
+  double bg, bg_p, img, img_p;
+};
+
+template <int NB, bool VISC>
+__device__ __forceinline__ void pvt(const Params& P, const Table& T, double p, double x, int flag, Pvt& f) {
   const double t = p - P.p_ref;
-  // water
-  const double bw = P.bw_ref * fma(P.cw, t, 1.0);
-  const double bw_p = P.bw_ref * P.cw;
-  // oil (and gas) from the table
-  double bo, bo_p, bo_x, imo, imo_p, imo_x, rs, rs_p, rs_x, sg, sg_x;
-  double bg = 0.0, bg_p = 0.0, img = 0.0, img_p = 0.0;
+  f.bw = P.bw_ref * fma(P.cw, t, 1.0);
+  f.bw_p = P.bw_p;
   const int kp = segment(T.pkey, T.nrow, dkey(p));
   const double dpk = p - T.p[kp];
+  f.imo = f.imo_p = f.imo_x = 0.0;
+  f.bg = f.bg_p = f.img = f.img_p = 0.0;
   if (NB == 3 && flag == 1) {
     const int kr = segment(T.rskey, T.nrow, dkey(x));
     const double pb = fma(x - T.rs[kr], T.q[kr], T.p[kr]);
@@ -182,38 +190,89 @@ __device__ __forceinline__ void cell_quantities(const Params& P, const Table& T,
     const double dpb = pb - T.p[kr];
     const double dp = p - pb;
     const double bsat = fma(dpb, T.s[0][kr], T.y[0][kr]);
-    const double isat = fma(dpb, T.s[1][kr], T.y[1][kr]);
     const double fb = fma(P.co, dp, 1.0);
-    const double fm = fma(-P.cmu, dp, 1.0);
-    bo = bsat * fb;
-    bo_p = bsat * P.co;
-    bo_x = (T.s[0][kr] * fb - bsat * P.co) * pb_x;
-    imo = isat * fm;
-    imo_p = -isat * P.cmu;
-    imo_x = (T.s[1][kr] * fm + isat * P.cmu) * pb_x;
-    rs = x; rs_p = 0.0; rs_x = 1.0;
-    sg = 0.0; sg_x = 0.0;
-  } else {
-    bo = fma(dpk, T.s[0][kp], T.y[0][kp]);
-    bo_p = T.s[0][kp]; bo_x = 0.0;
-    imo = fma(dpk, T.s[1][kp], T.y[1][kp]);
-    imo_p = T.s[1][kp]; imo_x = 0.0;
-    if (NB == 3) {
-      rs = fma(dpk, T.s[4][kp], T.y[4][kp]);
-      rs_p = T.s[4][kp];
-    } else {
-      rs = 0.0; rs_p = 0.0;
+    f.bo = bsat * fb;
+    f.bo_p = bsat * P.co;
+    f.bo_x = (T.s[0][kr] * fb - f.bo_p) * pb_x;
+    if (VISC) {
+      const double isat = fma(dpb, T.s[1][kr], T.y[1][kr]);
+      const double fm = fma(-P.cmu, dp, 1.0);
+      f.imo = isat * fm;
+      f.imo_p = -isat * P.cmu;
+      f.imo_x = (T.s[1][kr] * fm - f.imo_p) * pb_x;
     }
-    rs_x = 0.0;
-    sg = (NB == 3) ? x : 0.0;
-    sg_x = (NB == 3) ? 1.0 : 0.0;
+    f.rs = x; f.rs_p = 0.0; f.rs_x = 1.0;
+    f.sg = 0.0; f.sg_x = 0.0;
+  } else {
+    f.bo = fma(dpk, T.s[0][kp], T.y[0][kp]);
+    f.bo_p = T.s[0][kp]; f.bo_x = 0.0;
+    if (VISC) {
+      f.imo = fma(dpk, T.s[1][kp], T.y[1][kp]);
+      f.imo_p = T.s[1][kp];
+    }
+    if (NB == 3) {
+      f.rs = fma(dpk, T.s[4][kp], T.y[4][kp]);
+      f.rs_p = T.s[4][kp];
+      f.sg = x; f.sg_x = 1.0;
+    } else {
+      f.rs = 0.0; f.rs_p = 0.0;
+      f.sg = 0.0; f.sg_x = 0.0;
+    }
+    f.rs_x = 0.0;
   }
   if (NB == 3) {
-    bg = fma(dpk, T.s[2][kp], T.y[2][kp]);
-    bg_p = T.s[2][kp];
-    img = fma(dpk, T.s[3][kp], T.y[3][kp]);
-    img_p = T.s[3][kp];
+    f.bg = fma(dpk, T.s[2][kp], T.y[2][kp]);
+    f.bg_p = T.s[2][kp];
+    if (VISC) {
+      f.img = fma(dpk, T.s[3][kp], T.y[3][kp]);
+      f.img_p = T.s[3][kp];
+    }
   }
+}
+
+// Component amounts per bulk volume, phi S b (eq. 4 in black-oil form), and
+// with DERIV their derivatives with respect to (p, S_w, X).  Used for both
+// time levels, so that an unchanged state gives an exactly zero accumulation.
+template <int NB, bool DERIV>
+__device__ __forceinline__ void masses(const Params& P, const Pvt& f, double p, double sw, double phi_ref,
+                                       double* m, double* m_p, double* m_sw, double* m_x) {
+  const double phi = phi_ref * fma(P.cr, p - P.p_ref, 1.0);
+  const double so = (NB == 3) ? (1.0 - sw - f.sg) : (1.0 - sw);
+  const double sob = so * f.bo;
+  m[0] = phi * sw * f.bw;
+  m[1] = phi * sob;
+  if (NB == 3) m[2] = phi * fma(f.sg, f.bg, f.rs * sob);
+  if (DERIV) {
+    const double phi_p = phi_ref * P.cr;
+    const double so_x = -f.sg_x;
+    m_p[0] = fma(phi_p * sw, f.bw, phi * sw * f.bw_p);
+    m_sw[0] = phi * f.bw;
+    m_x[0] = 0.0;
+    m_p[1] = fma(phi_p, sob, phi * so * f.bo_p);
+    m_sw[1] = -phi * f.bo;
+    m_x[1] = phi * fma(so_x, f.bo, so * f.bo_x);
+    if (NB == 3) {
+      const double G = fma(f.sg, f.bg, f.rs * sob);
+      const double G_p = fma(f.sg, f.bg_p, fma(f.rs_p, sob, f.rs * so * f.bo_p));
+      const double G_x = fma(f.sg_x, f.bg, fma(f.rs_x, sob, f.rs * fma(so_x, f.bo, so * f.bo_x)));
+      m_p[2] = fma(phi_p, G, phi * G_p);
+      m_sw[2] = -phi * f.rs * f.bo;
+      m_x[2] = phi * G_x;
+    }
+  }
+}
+
+// PVT, rock, Corey / Stone II, capillary pressure, densities and mobilities
+// of one cell (Bulk: PVT, SAT, ROCK modules, Sec. 3.2.3); with AUX also the
+// component amounts and (for injector cells) the total mobility.  The
+// amounts are phi_ref S b scaled by whatever factor phi_ref carries.
+template <int NB, bool AUX>
+__device__ __forceinline__ void cell_quantities(const Params& P, const Table& T, double p, double sw,
+                                                double x, int flag, double phi_ref, CellQ& q,
+                                                CellAux& a, bool injector = true) {
+  Pvt f;
+  pvt<NB, true>(P, T, p, x, flag, f);
+  const double sg = f.sg;
 
   // relative permeabilities (Corey; Stone II for oil with three phases)
   double s_w = (sw - P.swc) * P.inv_w, s_w_d = P.inv_w;
@@ -239,9 +298,9 @@ __device__ __forceinline__ void cell_quantities(const Params& P, const Table& T,
     krg_sg = P.krg_max * dg_ * s_g_d;
     // k_ro = kc [(k_row/kc + k_rw)(k_rog/kc + k_rg) - (k_rw + k_rg)], k_row/kc = s_ow^n
     const double A = pow_ + krw;
-    const double A_sw = dow_ * s_ow_d + krw_sw;
+    const double A_sw = fma(dow_, s_ow_d, krw_sw);
     const double B = pog_ + krg;
-    const double B_sg = dog_ * s_og_d + krg_sg;
+    const double B_sg = fma(dog_, s_og_d, krg_sg);
     kro = P.kc * fma(A, B, -(krw + krg));
     kro_sw = P.kc * fma(A_sw, B, -krw_sw);
     kro_sg = P.kc * fma(A, B_sg, -krg_sg);
@@ -250,187 +309,194 @@ __device__ __forceinline__ void cell_quantities(const Params& P, const Table& T,
     kro = P.kc * pow_;
     kro_sw = P.kc * dow_ * s_ow_d;
   }
-  const double kro_x = kro_sg * sg_x;
-  const double krg_x = krg_sg * sg_x;
+  // X is S_g only in saturated cells (sg_x is 1 there and 0 otherwise)
+  const bool gx = (NB == 3) && (flag == 0);
+  const double kro_x = gx ? kro_sg : 0.0;
+  const double krg_x = gx ? krg_sg : 0.0;
 
   // capillary pressures: p_w = p - Pc_ow(S_w), p_g = p + Pc_go(S_g)
   const double omw = 1.0 - s_w;
   q.p = p;
   q.pw = p - P.pcow_max * (omw * omw);
-  q.dpw_sw = 2.0 * P.pcow_max * omw * s_w_d;
+  q.dpw_sw = P.pcow2 * omw * s_w_d;
   if (NB == 3) {
     q.pg = p + P.pcgo_max * (s_g * s_g);
-    q.dpg_x = 2.0 * P.pcgo_max * s_g * s_g_d * sg_x;
+    q.dpg_x = gx ? P.pcgo2 * s_g * s_g_d : 0.0;
   }
 
   // densities
-  q.rw = bw * P.rho_wsc;
-  q.rw_p = bw_p * P.rho_wsc;
-  const double ro0 = fma(rs, P.cg, P.rho_osc);
-  q.ro = ro0 * bo;
-  q.ro_p = fma(P.cg * rs_p, bo, ro0 * bo_p);
-  q.ro_x = fma(P.cg * rs_x, bo, ro0 * bo_x);
+  q.rw = f.bw * P.rho_wsc;
+  q.rw_p = P.rw_p;
+  const double ro0 = fma(f.rs, P.cg, P.rho_osc);
+  q.ro = ro0 * f.bo;
+  q.ro_p = fma(P.cg * f.rs_p, f.bo, ro0 * f.bo_p);
+  q.ro_x = fma(P.cg * f.rs_x, f.bo, ro0 * f.bo_x);
   if (NB == 3) {
-    q.rg = bg * P.cg;
-    q.rg_p = bg_p * P.cg;
+    q.rg = f.bg * P.cg;
+    q.rg_p = f.bg_p * P.cg;
   }
 
   // mobilities lambda = k_r * b / mu
-  const double bmw = bw * P.imu_w;
+  const double bmw = f.bw * P.imu_w;
   q.lw = krw * bmw;
-  q.lw_p = krw * (bw_p * P.imu_w);
+  q.lw_p = krw * P.bw_p_imu;
   q.lw_sw = krw_sw * bmw;
-  const double bmo = bo * imo;
-  const double bmo_p = fma(bo_p, imo, bo * imo_p);
-  const double bmo_x = fma(bo_x, imo, bo * imo_x);
+  const double bmo = f.bo * f.imo;
+  const double bmo_p = fma(f.bo_p, f.imo, f.bo * f.imo_p);
+  const double bmo_x = fma(f.bo_x, f.imo, f.bo * f.imo_x);
   q.lo = kro * bmo;
   q.lo_p = kro * bmo_p;
   q.lo_sw = kro_sw * bmo;
   q.lo_x = fma(kro_x, bmo, kro * bmo_x);
   if (NB == 3) {
-    const double bmg = bg * img;
+    const double bmg = f.bg * f.img;
     q.lg = krg * bmg;
-    q.lg_p = krg * fma(bg_p, img, bg * img_p);
+    q.lg_p = krg * fma(f.bg_p, f.img, f.bg * f.img_p);
     q.lg_x = krg_x * bmg;
-    q.rs = rs; q.rs_p = rs_p; q.rs_x = rs_x;
+    q.rs = f.rs; q.rs_p = f.rs_p; q.rs_x = f.rs_x;
   }
 
   if (AUX) {
-    // component amounts per bulk volume (eq. 4, black-oil form)
-    const double fr = fma(P.cr, t, 1.0);
-    const double phi = phi_ref * fr;
-    const double phi_p = phi_ref * P.cr;
-    const double so = (NB == 3) ? (1.0 - sw - sg) : (1.0 - sw);
-    const double so_x = -sg_x;
-    a.m[0] = phi * sw * bw;
-    a.m_p[0] = fma(phi_p * sw, bw, phi * sw * bw_p);
-    a.m_sw[0] = phi * bw;
-    a.m_x[0] = 0.0;
-    const double sob = so * bo;
-    a.m[1] = phi * sob;
-    a.m_p[1] = fma(phi_p, sob, phi * so * bo_p);
-    a.m_sw[1] = -phi * bo;
-    a.m_x[1] = phi * fma(so_x, bo, so * bo_x);
-    if (NB == 3) {
-      const double G = fma(sg, bg, rs * sob);
-      const double G_p = fma(sg, bg_p, fma(rs_p, sob, rs * so * bo_p));
-      const double G_sw = -rs * bo;
-      const double G_x = fma(sg_x, bg, fma(rs_x, sob, rs * fma(so_x, bo, so * bo_x)));
-      a.m[2] = phi * G;
-      a.m_p[2] = fma(phi_p, G, phi * G_p);
-      a.m_sw[2] = phi * G_sw;
-      a.m_x[2] = phi * G_x;
-      a.mob = fma(krw, P.imu_w, fma(kro, imo, krg * img));
-      a.mob_p = fma(kro, imo_p, krg * img_p);
-      a.mob_sw = fma(krw_sw, P.imu_w, kro_sw * imo);
-      a.mob_x = fma(kro_x, imo, fma(kro, imo_x, krg_x * img));
-      a.bg = bg; a.bg_p = bg_p;
+    masses<NB, true>(P, f, p, sw, phi_ref, a.m, a.m_p, a.m_sw, a.m_x);
+    a.mob = a.mob_p = a.mob_sw = a.mob_x = 0.0;
+    if (!injector) {
+    } else if (NB == 3) {
+      a.mob = fma(krw, P.imu_w, fma(kro, f.imo, krg * f.img));
+      a.mob_p = fma(kro, f.imo_p, krg * f.img_p);
+      a.mob_sw = fma(krw_sw, P.imu_w, kro_sw * f.imo);
+      a.mob_x = fma(kro_x, f.imo, fma(kro, f.imo_x, krg_x * f.img));
+      a.bg = f.bg; a.bg_p = f.bg_p;
     } else {
-      a.mob = fma(krw, P.imu_w, kro * imo);
-      a.mob_p = kro * imo_p;
-      a.mob_sw = fma(krw_sw, P.imu_w, kro_sw * imo);
+      a.mob = fma(krw, P.imu_w, kro * f.imo);
+      a.mob_p = kro * f.imo_p;
+      a.mob_sw = fma(krw_sw, P.imu_w, kro_sw * f.imo);
       a.mob_x = 0.0;
     }
-    a.bw = bw; a.bw_p = bw_p;
+    a.bw = f.bw; a.bw_p = f.bw_p;
   }
 }
 
-// Component amounts (values only) at the old time level.
-template <int NB>
+// Component amounts only (values, or values and derivatives), for the old
+// time level and for the adjoint; no saturation functions are needed there.
+template <int NB, bool DERIV>
 __device__ __forceinline__ void cell_masses(const Params& P, const Table& T, double p, double sw,
-                                            double x, int flag, double phi_ref, double* m) {
-  CellQ q{};
-  CellAux a{};
-  cell_quantities<NB, true>(P, T, p, sw, x, flag, phi_ref, q, a);
-  for (int e = 0; e < NB; ++e) m[e] = a.m[e];
+                                            double x, int flag, double phi_ref, double* m,
+                                            double* m_p = nullptr, double* m_sw = nullptr,
+                                            double* m_x = nullptr) {
+  Pvt f;
+  pvt<NB, false>(P, T, p, x, flag, f);
+  masses<NB, DERIV>(P, f, p, sw, phi_ref, m, m_p, m_sw, m_x);
 }
 
 // ---------------------------------------------------------------- face flux
+// Sign flip without an FP64 instruction.
+__device__ __forceinline__ double neg(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
+// One phase across one face: F = T lambda_up dphi with dphi = (pa_i - pa_j)
+// - gbar (z_i - z_j), gbar = g (rho_i + rho_j) / 2, and its derivatives in
+// the unknowns (p, S_w, X) of both cells.  `hz` = g (z_i - z_j) / 2; on
+// horizontal faces (GRAV false) it is zero and the gravity arithmetic is not
+// emitted.  The flags say which dependencies exist, so structural zeros cost
+// no FP64 instruction:
+//   PSW  the phase pressure depends on S_w (water, through Pc_ow), d = dpa;
+//   PX   the phase pressure depends on X (gas, through Pc_go), d = dpa;
+//   RX   the density depends on X (oil, through R_s);
+//   LSW, LX  the mobility depends on S_w, X.
+template <bool GRAV, bool PSW, bool PX, bool RX, bool LSW, bool LX>
+__device__ __forceinline__ void phase_flux(double T, double hz, double pa_i, double pa_j, double dpa_i,
+                                           double dpa_j, double rho_i, double rho_j, double rho_p_i,
+                                           double rho_p_j, double rho_x_i, double rho_x_j, double l_i,
+                                           double l_j, double l_p_i, double l_p_j, double l_sw_i,
+                                           double l_sw_j, double l_x_i, double l_x_j, double& F,
+                                           double (&di)[3], double (&dj)[3], bool& up) {
+  double dphi = pa_i - pa_j;
+  if (GRAV) dphi = fma(-(rho_i + rho_j), hz, dphi);
+  up = nonneg(dphi);
+  const double Tl = T * sel(up, l_i, l_j);
+  const double Td = T * dphi;
+  F = Tl * dphi;
+  const double ulp = Td * sel(up, l_p_i, l_p_j);
+  if (GRAV) {
+    di[0] = fma(Tl, fma(-rho_p_i, hz, 1.0), sel(up, ulp, 0.0));
+    dj[0] = fma(Tl, fma(-rho_p_j, hz, -1.0), sel(up, 0.0, ulp));
+  } else {
+    di[0] = Tl + sel(up, ulp, 0.0);
+    dj[0] = sel(up, 0.0, ulp) - Tl;
+  }
+  double usw = 0.0;
+  if (LSW) usw = Td * sel(up, l_sw_i, l_sw_j);
+  if (PSW) {
+    di[1] = fma(Tl, dpa_i, sel(up, usw, 0.0));
+    dj[1] = fma(neg(Tl), dpa_j, sel(up, 0.0, usw));
+  } else {
+    di[1] = sel(up, usw, 0.0);
+    dj[1] = sel(up, 0.0, usw);
+  }
+  double ux = 0.0;
+  if (LX) ux = Td * sel(up, l_x_i, l_x_j);
+  constexpr bool CX = PX || (GRAV && RX);   // dphi depends on X
+  if (CX) {
+    double cx_i, cx_j;
+    if (PX) {
+      cx_i = dpa_i;
+      cx_j = neg(dpa_j);
+    } else {
+      cx_i = neg(rho_x_i * hz);
+      cx_j = neg(rho_x_j * hz);
+    }
+    di[2] = fma(Tl, cx_i, sel(up, ux, 0.0));
+    dj[2] = fma(Tl, cx_j, sel(up, 0.0, ux));
+  } else {
+    di[2] = sel(up, ux, 0.0);
+    dj[2] = sel(up, 0.0, ux);
+  }
+}
+
 // Flux of every component across one face (i -> j, j the + neighbour) and
 // its derivatives with respect to both cells' unknowns (BulkConn, Sec. 3.2.4;
 // Darcy's law eq. 2 in two-point form, phase-upwinded).
 template <int NB>
 struct FaceOut {
   double F[NB];
-  double di[NB][NB];   // dF_e / du_i[v]
-  double dj[NB][NB];   // dF_e / du_j[v]
+  double di[NB][3];   // dF_e / du_i[v]
+  double dj[NB][3];   // dF_e / du_j[v]
 };
-
-// One phase: F = T lambda_up dphi, dphi = (pa_i - pa_j) - gbar (z_i - z_j),
-// gbar = g (rho_i + rho_j)/2.  `hz` = 0.5 g (z_i - z_j) (zero on horizontal
-// faces, where GRAV is false and the gravity arithmetic is skipped).
-// Outputs the flux and its derivatives in the local variables
-// (p, S_w, X) of i and j.
-template <bool GRAV>
-__device__ __forceinline__ void phase_flux(double T, double hz, double pa_i, double pa_j,
-                                           double rho_i, double rho_j,
-                                           // d pa / d(p, S_w, X) of each side
-                                           double pa_sw_i, double pa_x_i, double pa_sw_j, double pa_x_j,
-                                           // d rho / d(p, X) of each side
-                                           double rho_p_i, double rho_x_i, double rho_p_j, double rho_x_j,
-                                           // lambda and derivatives of each side
-                                           double l_i, double l_p_i, double l_sw_i, double l_x_i,
-                                           double l_j, double l_p_j, double l_sw_j, double l_x_j,
-                                           double& F, double* di, double* dj, bool& up_i) {
-  double dphi = pa_i - pa_j;
-  if (GRAV) dphi = fma(-(rho_i + rho_j), hz, dphi);
-  up_i = nonneg(dphi);
-  const double lu = sel(up_i, l_i, l_j);
-  const double Tl = T * lu;
-  const double Td = T * dphi;
-  F = Tl * dphi;
-  // derivative of dphi
-  double dp_i = 1.0, dp_j = -1.0, dx_i = pa_x_i, dx_j = -pa_x_j;
-  if (GRAV) {
-    dp_i = fma(-rho_p_i, hz, 1.0);
-    dp_j = fma(-rho_p_j, hz, -1.0);
-    dx_i = fma(-rho_x_i, hz, dx_i);
-    dx_j = fma(-rho_x_j, hz, dx_j);
-  }
-  // upwind mobility derivatives go to the upstream side only
-  const double ulp = Td * sel(up_i, l_p_i, l_p_j);
-  const double ulsw = Td * sel(up_i, l_sw_i, l_sw_j);
-  const double ulx = Td * sel(up_i, l_x_i, l_x_j);
-  di[0] = fma(Tl, dp_i, sel(up_i, ulp, 0.0));
-  dj[0] = fma(Tl, dp_j, sel(up_i, 0.0, ulp));
-  di[1] = fma(Tl, pa_sw_i, sel(up_i, ulsw, 0.0));
-  dj[1] = fma(-Tl, pa_sw_j, sel(up_i, 0.0, ulsw));
-  di[2] = fma(Tl, dx_i, sel(up_i, ulx, 0.0));
-  dj[2] = fma(Tl, dx_j, sel(up_i, 0.0, ulx));
-}
 
 template <int NB, bool GRAV>
 __device__ __forceinline__ void face_terms(double T, double hz, const CellQ& a, const CellQ& b,
-                                          FaceOut<NB>& o) {
-  double dw_i[3], dw_j[3], do_i[3], do_j[3];
+                                           FaceOut<NB>& o) {
   bool up_w, up_o;
-  // water: p_w = p - Pc_ow(S_w); rho_w depends on p only
-  phase_flux<GRAV>(T, hz, a.pw, b.pw, a.rw, b.rw, a.dpw_sw, 0.0, b.dpw_sw, 0.0, a.rw_p, 0.0, b.rw_p, 0.0,
-                   a.lw, a.lw_p, a.lw_sw, 0.0, b.lw, b.lw_p, b.lw_sw, 0.0, o.F[0], dw_i, dw_j, up_w);
-  // oil: p_o = p; rho_o depends on p and X
-  phase_flux<GRAV>(T, hz, a.p, b.p, a.ro, b.ro, 0.0, 0.0, 0.0, 0.0, a.ro_p, a.ro_x, b.ro_p, b.ro_x,
-                   a.lo, a.lo_p, a.lo_sw, a.lo_x, b.lo, b.lo_p, b.lo_sw, b.lo_x, o.F[1], do_i, do_j, up_o);
-  for (int v = 0; v < NB; ++v) {
-    o.di[0][v] = dw_i[v]; o.dj[0][v] = dw_j[v];
-    o.di[1][v] = do_i[v]; o.dj[1][v] = do_j[v];
-  }
+  // water: p_w = p - Pc_ow(S_w); rho_w and lambda_w depend on p and S_w
+  phase_flux<GRAV, true, false, false, true, false>(T, hz, a.pw, b.pw, a.dpw_sw, b.dpw_sw, a.rw, b.rw,
+                                                     a.rw_p, b.rw_p, 0.0, 0.0, a.lw, b.lw, a.lw_p, b.lw_p,
+                                                     a.lw_sw, b.lw_sw, 0.0, 0.0, o.F[0], o.di[0], o.dj[0],
+                                                     up_w);
+  // oil: p_o = p; rho_o and lambda_o depend on X only with three phases
+  phase_flux<GRAV, false, false, NB == 3, true, NB == 3>(T, hz, a.p, b.p, 0.0, 0.0, a.ro, b.ro, a.ro_p,
+                                                          b.ro_p, a.ro_x, b.ro_x, a.lo, b.lo, a.lo_p, b.lo_p,
+                                                          a.lo_sw, b.lo_sw, a.lo_x, b.lo_x, o.F[1], o.di[1],
+                                                          o.dj[1], up_o);
   if (NB == 3) {
-    double dg_i[3], dg_j[3];
+    double Fg, dg_i[3], dg_j[3];
     bool up_g;
-    phase_flux<GRAV>(T, hz, a.pg, b.pg, a.rg, b.rg, 0.0, a.dpg_x, 0.0, b.dpg_x, a.rg_p, 0.0, b.rg_p, 0.0,
-                     a.lg, a.lg_p, 0.0, a.lg_x, b.lg, b.lg_p, 0.0, b.lg_x, o.F[NB - 1], dg_i, dg_j, up_g);
+    // gas: p_g = p + Pc_go(S_g); rho_g depends on p, lambda_g on p and X
+    phase_flux<GRAV, false, true, false, false, true>(T, hz, a.pg, b.pg, a.dpg_x, b.dpg_x, a.rg, b.rg,
+                                                       a.rg_p, b.rg_p, 0.0, 0.0, a.lg, b.lg, a.lg_p, b.lg_p,
+                                                       0.0, 0.0, a.lg_x, b.lg_x, Fg, dg_i, dg_j, up_g);
     // gas component: free gas plus gas dissolved in the upstream oil
     const double rsu = sel(up_o, a.rs, b.rs);
     const double Fo = o.F[1];
-    o.F[NB - 1] = fma(rsu, Fo, o.F[NB - 1]);
+    o.F[NB - 1] = fma(rsu, Fo, Fg);
     const double frp = Fo * sel(up_o, a.rs_p, b.rs_p);
     const double frx = Fo * sel(up_o, a.rs_x, b.rs_x);
-    o.di[NB - 1][0] = fma(rsu, do_i[0], dg_i[0]) + sel(up_o, frp, 0.0);
-    o.dj[NB - 1][0] = fma(rsu, do_j[0], dg_j[0]) + sel(up_o, 0.0, frp);
-    o.di[NB - 1][1] = fma(rsu, do_i[1], dg_i[1]);
-    o.dj[NB - 1][1] = fma(rsu, do_j[1], dg_j[1]);
-    o.di[NB - 1][2] = fma(rsu, do_i[2], dg_i[2]) + sel(up_o, frx, 0.0);
-    o.dj[NB - 1][2] = fma(rsu, do_j[2], dg_j[2]) + sel(up_o, 0.0, frx);
+    o.di[NB - 1][0] = fma(rsu, o.di[1][0], dg_i[0]) + sel(up_o, frp, 0.0);
+    o.dj[NB - 1][0] = fma(rsu, o.dj[1][0], dg_j[0]) + sel(up_o, 0.0, frp);
+    o.di[NB - 1][1] = rsu * o.di[1][1];
+    o.dj[NB - 1][1] = rsu * o.dj[1][1];
+    o.di[NB - 1][2] = fma(rsu, o.di[1][2], dg_i[2]) + sel(up_o, frx, 0.0);
+    o.dj[NB - 1][2] = fma(rsu, o.dj[1][2], dg_j[2]) + sel(up_o, 0.0, frx);
   }
 }
 

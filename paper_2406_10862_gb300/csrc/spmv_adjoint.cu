@@ -1,8 +1,8 @@
 // Block-CSR products and the adjoint vector-Jacobian product.
 //
-// spmv_kernel       y = alpha A x + beta y on the grid's 7-point block pattern
+// spmv_grid_kernel  y = alpha A x + beta y on the grid's 7-point block pattern
 //                   (the kernel the linear solver iterates on, Sec. 3.3.3);
-// spmv_t_kernel     the transposed product, gathered through the mirror map
+// spmv_kernel<T>    the transposed product, gathered through the mirror map
 //                   (block (c, n) <-> block (n, c)) so that every output row is
 //                   owned by one thread and no atomics are needed;
 // vjp_kernel        lambda^T dR/d(u_new, u_old, ln k, phi) of the residual of
@@ -130,6 +130,62 @@ __global__ void __launch_bounds__(256) spmv_kernel(long long N, const int32_t* _
   }
 }
 
+// Product on the grid's own pattern, one thread per block row.  The FP64
+// FMAs (NB*NB per block) are the binding resource on GB300, so the kernel
+// is arranged to keep them fed: the columns come from the 7-point structure
+// (no col_idx -> x dependent loads), all x entries of the row are loaded
+// first, then each block is loaded and consumed.  Rows with missing
+// neighbours read x at their own cell instead and skip those blocks.
+template <int NB>
+__global__ void __launch_bounds__(256) spmv_grid_kernel(Params P, const int32_t* __restrict__ row_ptr,
+                                                        const double* __restrict__ val, double alpha,
+                                                        const double* __restrict__ x, double beta,
+                                                        double* __restrict__ y, int mode) {
+  constexpr int B2 = NB * NB;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.N) return;
+  bool has[7];
+  neighbours(P, c, has);
+  const long long off[7] = {-P.nxy, -P.nx, -1, 0, 1, P.nx, P.nxy};
+  int slot[7];
+  int s = 0;
+#pragma unroll
+  for (int t = 0; t < 7; ++t) {
+    slot[t] = s;
+    s += has[t];
+  }
+  double xv[7][NB];
+#pragma unroll
+  for (int t = 0; t < 7; ++t) {
+    const long long n = has[t] ? c + off[t] : c;
+#pragma unroll
+    for (int v = 0; v < NB; ++v) xv[t][v] = x[n * NB + v];
+  }
+  const double* row = val + (long long)row_ptr[c] * B2;
+  double acc[NB];
+#pragma unroll
+  for (int e = 0; e < NB; ++e) acc[e] = 0.0;
+#pragma unroll
+  for (int t = 0; t < 7; ++t) {
+    if (!has[t]) continue;
+    const double* blk = row + slot[t] * B2;
+    double b[B2];
+#pragma unroll
+    for (int q = 0; q < B2; ++q) b[q] = __ldg(blk + q);
+#pragma unroll
+    for (int e = 0; e < NB; ++e)
+#pragma unroll
+      for (int v = 0; v < NB; ++v) acc[e] = fma(b[e * NB + v], xv[t][v], acc[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < NB; ++e) {
+    double o = acc[e];
+    if (mode >= 1) o = alpha * o;
+    if (mode == 2) o = fma(beta, y[c * NB + e], o);
+    y[c * NB + e] = o;
+  }
+}
+
 // ------------------------------------------------------------------ adjoint
 template <int NB>
 __global__ void __launch_bounds__(256) vjp_kernel(Params P, const Table* __restrict__ gT,
@@ -183,31 +239,28 @@ __global__ void __launch_bounds__(256) vjp_kernel(Params P, const Table* __restr
   const int fn = (NB == 3) ? (f_new[c] & 1) : 0, fo = (NB == 3) ? (f_old[c] & 1) : 0;
   const double ph = phi[c];
 
-  if (g_uold || g_phi) {
-    CellQ q{};
-    CellAux ao{};
-    cell_quantities<NB, true>(P, T, po, swo, xo, fo, ph, q, ao);
-    if (g_uold) {
-      double g[3] = {0.0, 0.0, 0.0};
+  if (g_uold) {
+    double m[3], m_p[3], m_sw[3], m_x[3];
+    cell_masses<NB, true>(P, T, po, swo, xo, fo, ph, m, m_p, m_sw, m_x);
+    double g[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-      for (int e = 0; e < NB; ++e) {
-        g[0] = fma(lc[e], ao.m_p[e], g[0]);
-        g[1] = fma(lc[e], ao.m_sw[e], g[1]);
-        g[2] = fma(lc[e], ao.m_x[e], g[2]);
-      }
-#pragma unroll
-      for (int v = 0; v < NB; ++v) g_uold[v * N + c] = -scale * g[v];
+    for (int e = 0; e < NB; ++e) {
+      g[0] = fma(lc[e], m_p[e], g[0]);
+      g[1] = fma(lc[e], m_sw[e], g[1]);
+      g[2] = fma(lc[e], m_x[e], g[2]);
     }
-    if (g_phi) {
-      // the accumulation is linear in the reference porosity
-      double mn[3], mo[3];
-      cell_masses<NB>(P, T, pn, swn, xn, fn, 1.0, mn);
-      cell_masses<NB>(P, T, po, swo, xo, fo, 1.0, mo);
-      double g = 0.0;
 #pragma unroll
-      for (int e = 0; e < NB; ++e) g = fma(lc[e], mn[e] - mo[e], g);
-      g_phi[c] = scale * g;
-    }
+    for (int v = 0; v < NB; ++v) g_uold[v * N + c] = -scale * g[v];
+  }
+  if (g_phi) {
+    // the accumulation is linear in the reference porosity
+    double mn[3], mo[3];
+    cell_masses<NB, false>(P, T, pn, swn, xn, fn, 1.0, mn);
+    cell_masses<NB, false>(P, T, po, swo, xo, fo, 1.0, mo);
+    double g = 0.0;
+#pragma unroll
+    for (int e = 0; e < NB; ++e) g = fma(lc[e], mn[e] - mo[e], g);
+    g_phi[c] = scale * g;
   }
 
   if (g_lnk) {
@@ -288,10 +341,10 @@ cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, cons
   const int mode = (beta != 0.0) ? 2 : (alpha != 1.0 ? 1 : 0);
   if (g->prm.nb == 3) {
     if (transpose) spmv_kernel<3, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
-    else spmv_kernel<3, false><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+    else spmv_grid_kernel<3><<<blocks, 256, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
   } else {
     if (transpose) spmv_kernel<2, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
-    else spmv_kernel<2, false><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+    else spmv_grid_kernel<2><<<blocks, 256, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
   }
   return cudaGetLastError();
 }
