@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "OCP_OK", 1: "OCP_ERR_INVALID_ARG", 2: "OCP_ERR_CUDA", 3: "OC
 
 # Every symbol the header declares; the CPU tests check the library exports them.
 EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_pattern", "ocp_linearize",
-           "ocp_linearize_noalloc", "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
+           "ocp_linearize_noalloc", "ocp_probe_fp64", "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
 
 
 class OcpError(RuntimeError):
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = False):
     lib.ocp_adjoint_vjp.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.ocp_well_rates.argtypes = [vp, vp, vp, vp, vp]
     lib.ocp_get_status.argtypes = [vp, vp]
+    lib.ocp_probe_fp64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.ocp_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "ocp_last_error":
@@ -280,6 +281,14 @@ class Grid:
     def status(self, stream=None):
         """Synchronise and return the sticky device status (an int, 0 = OK)."""
         return load().ocp_get_status(self._h, _stream(self.device, stream))
+
+
+def probe_fp64(device=0, reps=3):
+    """Sustained FP64 FMA rate of the device in GFLOP/s (``ocp_probe_fp64``)."""
+    lib = load()
+    r = ctypes.c_double()
+    _check(lib.ocp_probe_fp64(int(device), int(reps), ctypes.byref(r)))
+    return 2.0 * r.value / 1e9
 
 
 # C names, for callers who prefer the flat interface
