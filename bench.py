@@ -367,6 +367,8 @@ def run_gpu(args, rank, world, local_rank):
             "clocks": clk.summary(),
             "device_status": st,
         }
+        if not args.no_ensemble:
+            line["ensemble"] = run_ensemble(dev, local_rank, reps=max(5, min(args.steps, 20)))
         if world == 1 and not args.no_cpu_baseline:
             t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s)
             cpu = 1e-6 / cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp)
@@ -376,6 +378,69 @@ def run_gpu(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_ensemble(dev, local_rank, reps=10):
+    """The 64-model ensemble (cell counts log-uniform in 2e4..4e5, ~8.1 M cells):
+    one batched pass (tuned launch shape, CUDA graph) against 64 separate
+    ocp_linearize calls on the same stream; both must give identical bits."""
+    import numpy as np
+    import torch
+
+    from paper_2406_10862_gb300 import autotune, ocp, workloads as W
+
+    models = W.ensemble()
+    grids, ios = [], []
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    for g, s in models:
+        grid = ocp.Grid(g, local_rank)
+        grids.append(grid)
+        ios.append(dict(u_new=T(s.u_new.ravel()), flag_new=T(s.flag_new), u_old=T(s.u_old.ravel()),
+                        flag_old=T(s.flag_old),
+                        residual=torch.empty(grid.nb * grid.N, dtype=torch.float64, device=dev),
+                        bsr_val=torch.empty(grid.nnzb * grid.nb ** 2, dtype=torch.float64, device=dev)))
+    dt = models[0][1].dt
+    ncell = sum(g.N for g in grids)
+    batch = ocp.Batch(grids)
+    batch.set_io(ios)
+    shape, cached = autotune.tuned_shape(batch, dt)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 2 ** 20 // 8, dtype=torch.float64, device=dev)
+
+    def per_model():
+        for grid, io in zip(grids, ios):
+            grid.linearize(io["u_new"], io["flag_new"], io["u_old"], io["flag_old"], dt, io["residual"],
+                           io["bsr_val"])
+
+    def batched():
+        batch.linearize(dt, graph=True)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    t_sep = timed(per_model)
+    ref = [(io["residual"].clone(), io["bsr_val"].clone()) for io in ios]
+    t_bat = timed(batched)
+    same = all(torch.equal(io["residual"].view(torch.int64), r.view(torch.int64)) and
+               torch.equal(io["bsr_val"].view(torch.int64), v.view(torch.int64)) for io, (r, v) in zip(ios, ref))
+    st = batch.status()
+    return {"workload": "64 black-oil boxes, cell counts log-uniform in 2e4..4e5", "models": len(grids),
+            "cells": ncell, "per_model_ms": t_sep, "batched_graph_ms": t_bat,
+            "per_model_mcells": ncell / (t_sep * 1e-3) / 1e6, "batched_mcells": ncell / (t_bat * 1e-3) / 1e6,
+            "speedup": t_sep / t_bat, "bitwise_equal": bool(same), "device_status": st,
+            "launch_shape": shape, "shape_from_cache": cached, "launches_per_model_path": 3 * len(grids),
+            "launches_batched": 3}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,6 +448,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-model batched-ensemble measurement")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, no CPU baseline): the command profiled by ncu")
     args = ap.parse_args()

@@ -179,6 +179,70 @@ ocp_status ocp_adjoint_vjp(ocp_grid* grid, const double* u_new, const int8_t* fl
 ocp_status ocp_well_rates(ocp_grid* grid, const double* u, const int8_t* flag, double* q,
                           void* cuda_stream);
 
+/* ---------------------------------------------------------------- batches
+ * An ensemble of grids linearised together (the same arithmetic as calling
+ * ocp_linearize on each grid, bit for bit).  The three stages of the
+ * linearisation -- cell properties with accumulation and wells (Bulk and
+ * AllWells, Secs. 3.2.3-3.2.4), faces (BulkConn), assembly (LinearSystem,
+ * Sec. 3.3.3) -- each run as one launch over a tile list of every grid's
+ * cells, largest grids first, so small grids no longer leave most of the GPU
+ * idle.  The paper partitions one grid over MPI ranks instead; batching
+ * independent models on one GPU has no counterpart in it. */
+typedef struct ocp_batch ocp_batch;
+
+/* Device pointers of one model's inputs and outputs, as for ocp_linearize. */
+typedef struct {
+  const double* u_new;
+  const int8_t* flag_new;
+  const double* u_old;
+  const int8_t* flag_old;
+  double* residual;
+  double* bsr_val;
+  double* face_flux;      /* may be NULL */
+} ocp_batch_io;
+
+/* Launch shape of the three stages (0 cell, 1 face, 2 assembly): cells per
+ * tile (128 or 256; one thread per cell) and CTAs per SM of a persistent
+ * launch (1..64), or 0 for one CTA per tile.  Results do not depend on it. */
+typedef struct {
+  int cells_per_tile[3];
+  int ctas_per_sm[3];
+} ocp_launch_shape;
+
+/* Groups n >= 1 grids (same device, same number of phases; each grid may
+ * appear once).  Allocates the argument table and tile lists.  The grids
+ * must outlive the batch; ocp_linearize on a member grid while a batch call
+ * on it is in flight races on the grid's scratch. */
+ocp_status ocp_batch_create(ocp_grid* const* grids, int n, ocp_batch** out);
+ocp_status ocp_batch_destroy(ocp_batch* batch);      /* NULL is accepted */
+
+/* Sets every model's input/output device pointers (host array io[n]).
+ * Synchronises the device. */
+ocp_status ocp_batch_set_io(ocp_batch* batch, const ocp_batch_io* io);
+
+/* Linearises every model for the step dt (three launches on the stream).
+ * When dt differs from the previous call the argument table is re-uploaded,
+ * which synchronises the stream. */
+ocp_status ocp_batch_linearize(ocp_batch* batch, double dt, void* cuda_stream);
+
+/* Same as ocp_batch_linearize, but the three launches are captured once (on
+ * a private stream) into a CUDA graph that is replayed on cuda_stream. */
+ocp_status ocp_batch_graph_launch(ocp_batch* batch, double dt, void* cuda_stream);
+
+/* Autotuner: times every stage with 2 tile sizes x 6 grid sizes (median of
+ * reps after a warm-up) and keeps the fastest per stage; returns it in *best
+ * (may be NULL).  Synchronises the stream many times. */
+ocp_status ocp_batch_tune(ocp_batch* batch, double dt, int reps, ocp_launch_shape* best, void* cuda_stream);
+ocp_status ocp_batch_set_shape(ocp_batch* batch, const ocp_launch_shape* shape);
+ocp_status ocp_batch_get_shape(const ocp_batch* batch, ocp_launch_shape* shape);
+
+/* Sticky device status of every member grid (see ocp_get_status). */
+ocp_status ocp_batch_get_status(ocp_batch* batch, void* cuda_stream);
+
+/* Launch shape of ocp_linearize on one grid (for example one found by
+ * ocp_batch_tune on a batch of that grid alone). */
+ocp_status ocp_grid_set_shape(ocp_grid* grid, const ocp_launch_shape* shape);
+
 /* Synchronises the stream, then returns and clears the grid's sticky device
  * status (OCP_OK if no kernel reported a problem since the last call). */
 ocp_status ocp_get_status(ocp_grid* grid, void* cuda_stream);

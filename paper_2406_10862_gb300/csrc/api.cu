@@ -229,6 +229,11 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   P.bw_p_imu = (d->bw_ref * d->cw) * P.imu_w;
   P.vol_rb = d->dx * d->dy * d->dz / ocp::kRbFt3;
 
+  for (int s = 0; s < 3; ++s) {
+    g->cfg.tpb[s] = 256;
+    g->cfg.ctas_per_sm[s] = 0;
+  }
+  g->sms = 0;
   g->nnzb = 7 * N - 2 * ((long long)d->ny * d->nz + (long long)d->nx * d->nz + (long long)d->nx * d->ny);
   g->scratch_doubles = ocp::linearize_scratch_doubles(N);
 
@@ -250,6 +255,7 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   OCP_ALLOC(g->d_scratch, sizeof(double) * g->scratch_doubles);
   OCP_ALLOC(d_lnk, sizeof(double) * N);
 #undef OCP_ALLOC
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_table, &T, sizeof(T), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_phi, d->phi, sizeof(double) * N, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_lnk, d->lnk, sizeof(double) * N, cudaMemcpyHostToDevice);

@@ -17,6 +17,13 @@
 // On GB300 the FP64 pipe, not HBM, bounds these kernels, so each face is
 // computed once and results travel through (coalesced, variable-major)
 // scratch rather than being recomputed.
+//
+// Every kernel walks a list of tiles -- TPB consecutive cells of one model --
+// with its CTAs striding over the list.  A single grid is the one-model case
+// (its arguments passed by value, tiles implied); a batch of grids passes a
+// device table of per-model arguments and an explicit tile list.  Both run
+// the same kernels, so a batched linearisation is bit-identical to the
+// per-grid one, whatever the tile size or the number of CTAs.
 #include "ocp_internal.cuh"
 #include "kernels.cuh"
 
@@ -53,34 +60,24 @@ __device__ __forceinline__ void load_q(const double* __restrict__ s, long long N
 }
 
 template <int NB>
-__global__ void __launch_bounds__(256) cell_kernel(Params P, const Table* __restrict__ gT,
-                                                   const double* __restrict__ u_new,
-                                                   const int8_t* __restrict__ f_new,
-                                                   const double* __restrict__ u_old,
-                                                   const int8_t* __restrict__ f_old,
-                                                   const double* __restrict__ phi,
-                                                   const int32_t* __restrict__ perf_of_cell,
-                                                   const Perf* __restrict__ perf, double scale,
-                                                   double* __restrict__ scr, int* status) {
-  __shared__ Table T;
-  for (int i = threadIdx.x; i < (int)(sizeof(Table) / 8); i += blockDim.x)
-    reinterpret_cast<double*>(&T)[i] = reinterpret_cast<const double*>(gT)[i];
-  __syncthreads();
+__device__ __forceinline__ void cell_body(const ModelArgs& M, const Table& T, long long c) {
+  const Params& P = M.P;
   const long long N = P.N;
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= N) return;
+  const double* __restrict__ u_new = M.u_new;
+  const double* __restrict__ u_old = M.u_old;
+  double* __restrict__ scr = M.scr;
   const double pn = u_new[c], swn = u_new[N + c], xn = (NB == 3) ? u_new[2 * N + c] : 0.0;
   const double po = u_old[c], swo = u_old[N + c], xo = (NB == 3) ? u_old[2 * N + c] : 0.0;
-  const int fn = (NB == 3) ? f_new[c] : 0, fo = (NB == 3) ? f_old[c] : 0;
+  const int fn = (NB == 3) ? M.f_new[c] : 0, fo = (NB == 3) ? M.f_old[c] : 0;
   int bad = 0;
   if (!(finite(pn) && finite(swn) && finite(xn) && finite(po) && finite(swo) && finite(xo))) bad |= kStatNonFinite;
   if ((unsigned)fn > 1u || (unsigned)fo > 1u) bad |= kStatBadFlag;
-  if (bad) atomicOr(status, bad);
+  if (bad) atomicOr(M.status, bad);
   // pore volume over dt folded into the porosity: the amounts come out as
   // accumulation terms directly
-  const double phs = phi[c] * scale;
-  const int ip = perf_of_cell[c];
-  const bool inj = ip >= 0 && perf[ip].kind == 1;
+  const double phs = M.phi[c] * M.scale;
+  const int ip = M.perf_of_cell[c];
+  const bool inj = ip >= 0 && M.perf[ip].kind == 1;
   CellQ q{};
   CellAux a{};
   cell_quantities<NB, true>(P, T, pn, swn, xn, fn & 1, phs, q, a, inj);
@@ -95,9 +92,8 @@ __global__ void __launch_bounds__(256) cell_kernel(Params P, const Table* __rest
     dg[e][2] = a.m_x[e];
   }
   if (ip >= 0) {
-    // the well terms need the true (unscaled) injector mobility only
     double src[3], ds[3][3];
-    well_source<NB>(perf[ip], q, a, src, ds);
+    well_source<NB>(M.perf[ip], q, a, src, ds);
     for (int e = 0; e < NB; ++e) {
       r[e] -= src[e];
       for (int v = 0; v < NB; ++v) dg[e][v] -= ds[e][v];
@@ -113,14 +109,14 @@ __global__ void __launch_bounds__(256) cell_kernel(Params P, const Table* __rest
 }
 
 template <int NB>
-__global__ void __launch_bounds__(256) face_kernel(Params P, const double* __restrict__ trans,
-                                                   const int32_t* __restrict__ row_ptr,
-                                                   double* __restrict__ scr, double* __restrict__ val,
-                                                   double* __restrict__ face_flux) {
+__device__ __forceinline__ void face_body(const ModelArgs& M, long long c) {
   constexpr int B2 = NB * NB;
+  const Params& P = M.P;
   const long long N = P.N;
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= N) return;
+  double* __restrict__ scr = M.scr;
+  double* __restrict__ val = M.val;
+  double* __restrict__ face_flux = M.face_flux;
+  const int32_t* __restrict__ row_ptr = M.row_ptr;
   const int i = (int)(c % P.nx);
   const int j = (int)((c / P.nx) % P.ny);
   const int k = (int)(c / P.nxy);
@@ -149,7 +145,7 @@ __global__ void __launch_bounds__(256) face_kernel(Params P, const double* __res
     CellQ b;
     load_q<NB>(scr, N, n, b);
     FaceOut<NB> o;
-    const double T = trans[d * N + c];
+    const double T = M.trans[d * N + c];
     if (d == 2) face_terms<NB, true>(T, -P.grav_dz, a, b, o);
     else face_terms<NB, false>(T, 0.0, a, b, o);
     // this row: flux out, diagonal, and the block of the + neighbour
@@ -188,13 +184,10 @@ __global__ void __launch_bounds__(256) face_kernel(Params P, const double* __res
 }
 
 template <int NB>
-__global__ void __launch_bounds__(256) assemble_kernel(Params P, const int32_t* __restrict__ row_ptr,
-                                                       const double* __restrict__ scr,
-                                                       double* __restrict__ res, double* __restrict__ val,
-                                                       int* status) {
+__device__ __forceinline__ void assemble_body(const ModelArgs& M, long long c) {
+  const Params& P = M.P;
   const long long N = P.N;
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= N) return;
+  const double* __restrict__ scr = M.scr;
   const int i = (int)(c % P.nx);
   const int j = (int)((c / P.nx) % P.ny);
   const int k = (int)(c / P.nxy);
@@ -217,30 +210,145 @@ __global__ void __launch_bounds__(256) assemble_kernel(Params P, const int32_t* 
       for (int v = 0; v < NB; ++v) dg[e][v] -= scr[(base + 3 + 3 * e + v) * N + c];
     }
   }
-  double* out = val + ((long long)row_ptr[c] + (int)hm[0] + (int)hm[1] + (int)hm[2]) * NB * NB;
+  double* out = M.val + ((long long)M.row_ptr[c] + (int)hm[0] + (int)hm[1] + (int)hm[2]) * NB * NB;
   bool ok = true;
 #pragma unroll
   for (int e = 0; e < NB; ++e) {
-    res[c * NB + e] = r[e];
+    M.res[c * NB + e] = r[e];
     ok = ok && finite(r[e]);
 #pragma unroll
     for (int v = 0; v < NB; ++v) out[e * NB + v] = dg[e][v];
   }
-  if (!ok) atomicOr(status, kStatNonFinite);
+  if (!ok) atomicOr(M.status, kStatNonFinite);
 }
 
-template <int NB>
-void launch_all(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
-                const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
-                double* face_flux, cudaStream_t s) {
-  const Params& P = g->prm;
-  const int threads = 256;
-  const unsigned blocks = (unsigned)((P.N + threads - 1) / threads);
-  const double scale = P.vol_rb / dt;
-  cell_kernel<NB><<<blocks, threads, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi,
-                                             g->d_perf_of_cell, g->d_perf, scale, scratch, g->d_status);
-  face_kernel<NB><<<blocks, threads, 0, s>>>(P, g->d_trans, g->d_row_ptr, scratch, val, face_flux);
-  assemble_kernel<NB><<<blocks, threads, 0, s>>>(P, g->d_row_ptr, scratch, res, val, g->d_status);
+// The model and first cell of tile t.
+template <int TPB>
+__device__ __forceinline__ const ModelArgs& tile_of(const TileList& L, const ModelArgs& single, int t,
+                                                     int& m, long long& c0) {
+  if (L.models) {
+    const int2 tt = L.tiles[t];
+    m = tt.x;
+    c0 = tt.y;
+    return L.models[m];
+  }
+  m = 0;
+  c0 = (long long)t * TPB;
+  return single;
+}
+
+template <int NB, int TPB>
+__global__ void __launch_bounds__(TPB, 512 / TPB) cell_kernel(TileList L, ModelArgs single) {
+  __shared__ Table T;
+  int cur = -1;
+  for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
+    int m;
+    long long c0;
+    const ModelArgs& M = tile_of<TPB>(L, single, t, m, c0);
+    if (m != cur) {                      // the PVT table of this tile's model
+      __syncthreads();
+      for (int i = threadIdx.x; i < (int)(sizeof(Table) / 8); i += TPB)
+        reinterpret_cast<double*>(&T)[i] = reinterpret_cast<const double*>(M.table)[i];
+      __syncthreads();
+      cur = m;
+    }
+    const long long c = c0 + threadIdx.x;
+    if (c < M.P.N) cell_body<NB>(M, T, c);
+  }
+}
+
+template <int NB, int TPB>
+__global__ void __launch_bounds__(TPB) face_kernel(TileList L, ModelArgs single) {
+  for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
+    int m;
+    long long c0;
+    const ModelArgs& M = tile_of<TPB>(L, single, t, m, c0);
+    const long long c = c0 + threadIdx.x;
+    if (c < M.P.N) face_body<NB>(M, c);
+  }
+}
+
+template <int NB, int TPB>
+__global__ void __launch_bounds__(TPB) assemble_kernel(TileList L, ModelArgs single) {
+  for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
+    int m;
+    long long c0;
+    const ModelArgs& M = tile_of<TPB>(L, single, t, m, c0);
+    const long long c = c0 + threadIdx.x;
+    if (c < M.P.N) assemble_body<NB>(M, c);
+  }
+}
+
+template <int NB, int TPB>
+void launch_stage(int stage, const TileList& L, const ModelArgs& single, int grid, cudaStream_t s) {
+  if (stage == 0) cell_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
+  else if (stage == 1) face_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
+  else assemble_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
+}
+
+}  // namespace
+
+// Launches the three stages.  `lists[0]` / `lists[1]` are the tile lists for
+// 128 / 256 cells per tile; cfg picks, per stage, the tile size and the grid
+// (CTAs per SM times the SM count, or 0 for one CTA per tile; a negative
+// count skips the stage, which only the autotuner uses).
+cudaError_t launch_tiles(int nb, const TileList* lists, const ModelArgs& single, const LaunchCfg& cfg,
+                         int sms, cudaStream_t s) {
+  for (int stage = 0; stage < 3; ++stage) {
+    if (cfg.ctas_per_sm[stage] < 0) continue;
+    const int tpb = cfg.tpb[stage] == 128 ? 128 : 256;
+    const TileList& L = lists[tpb == 128 ? 0 : 1];
+    if (L.ntiles == 0) continue;
+    int grid = cfg.ctas_per_sm[stage] > 0 ? cfg.ctas_per_sm[stage] * sms : L.ntiles;
+    if (grid > L.ntiles) grid = L.ntiles;
+    if (nb == 3) {
+      if (tpb == 128) launch_stage<3, 128>(stage, L, single, grid, s);
+      else launch_stage<3, 256>(stage, L, single, grid, s);
+    } else {
+      if (tpb == 128) launch_stage<2, 128>(stage, L, single, grid, s);
+      else launch_stage<2, 256>(stage, L, single, grid, s);
+    }
+  }
+  return cudaGetLastError();
+}
+
+ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
+                     const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
+                     double* face_flux) {
+  ModelArgs M;
+  M.P = g->prm;
+  M.table = g->d_table;
+  M.trans = g->d_trans;
+  M.row_ptr = g->d_row_ptr;
+  M.phi = g->d_phi;
+  M.perf_of_cell = g->d_perf_of_cell;
+  M.perf = g->d_perf;
+  M.status = g->d_status;
+  M.scr = scratch;
+  M.u_new = u_new;
+  M.f_new = f_new;
+  M.u_old = u_old;
+  M.f_old = f_old;
+  M.res = res;
+  M.val = val;
+  M.face_flux = face_flux;
+  M.scale = g->prm.vol_rb / dt;
+  return M;
+}
+
+namespace {
+
+cudaError_t launch_single(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
+                          const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
+                          double* face_flux, cudaStream_t s) {
+  const ModelArgs M = model_args(g, scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux);
+  TileList lists[2];
+  lists[0].models = nullptr;
+  lists[0].tiles = nullptr;
+  lists[0].ntiles = (int)((g->prm.N + 127) / 128);
+  lists[1] = lists[0];
+  lists[1].ntiles = (int)((g->prm.N + 255) / 256);
+  return launch_tiles(g->prm.nb, lists, M, g->cfg, g->sms, s);
 }
 
 }  // namespace
@@ -251,17 +359,13 @@ int64_t linearize_scratch_doubles(int64_t N) { return (int64_t)100 * N; }
 cudaError_t launch_linearize(const ocp_grid* g, const double* u_new, const int8_t* f_new,
                              const double* u_old, const int8_t* f_old, double dt, double* res,
                              double* val, double* face_flux, cudaStream_t s) {
-  if (g->prm.nb == 3) launch_all<3>(g, g->d_scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s);
-  else launch_all<2>(g, g->d_scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s);
-  return cudaGetLastError();
+  return launch_single(g, g->d_scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s);
 }
 
 cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const double* u_new,
                                      const int8_t* f_new, const double* u_old, const int8_t* f_old, double dt,
                                      double* res, double* val, double* face_flux, cudaStream_t s) {
-  if (g->prm.nb == 3) launch_all<3>(g, scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s);
-  else launch_all<2>(g, scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s);
-  return cudaGetLastError();
+  return launch_single(g, scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s);
 }
 
 }  // namespace ocp

@@ -70,6 +70,13 @@ struct Perf {
   double p_bh;
 };
 
+// Launch shape of the three linearisation stages (cell, face, assemble):
+// cells per tile (128 or 256) and CTAs per SM (0: one CTA per tile).
+struct LaunchCfg {
+  int tpb[3];
+  int ctas_per_sm[3];
+};
+
 }  // namespace ocp
 
 // The opaque handle of the C interface.
@@ -93,7 +100,43 @@ struct ocp_grid {
   int* d_status;             // sticky device status word
   double* d_scratch;         // per-cell scratch of the linearisation
   int64_t scratch_doubles;
+  ocp::LaunchCfg cfg;        // launch shape of the linearisation
+  int sms;                   // SM count of the device
 };
+
+namespace ocp {
+
+// Everything one model's linearisation reads and writes (device pointers).
+struct ModelArgs {
+  Params P;
+  const Table* table;
+  const double* trans;
+  const int32_t* row_ptr;
+  const double* phi;
+  const int32_t* perf_of_cell;
+  const Perf* perf;
+  int* status;
+  double* scr;
+  const double* u_new;
+  const int8_t* f_new;
+  const double* u_old;
+  const int8_t* f_old;
+  double* res;
+  double* val;
+  double* face_flux;
+  double scale;              // bulk volume in rb / dt
+};
+
+// Tiles of `TPB` consecutive cells: with models == nullptr the single model
+// passed by value, tile t starting at cell t * TPB; otherwise tiles[t] =
+// (model, first cell).
+struct TileList {
+  const ModelArgs* models;
+  const int2* tiles;
+  int ntiles;
+};
+
+}  // namespace ocp
 
 namespace ocp {
 

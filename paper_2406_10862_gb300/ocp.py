@@ -26,7 +26,10 @@ STATUS_NAMES = {0: "OCP_OK", 1: "OCP_ERR_INVALID_ARG", 2: "OCP_ERR_CUDA", 3: "OC
 
 # Every symbol the header declares; the CPU tests check the library exports them.
 EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_pattern", "ocp_linearize",
-           "ocp_linearize_noalloc", "ocp_probe_fp64", "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
+           "ocp_linearize_noalloc", "ocp_probe_fp64", "ocp_batch_create", "ocp_batch_destroy",
+           "ocp_batch_set_io", "ocp_batch_linearize", "ocp_batch_graph_launch", "ocp_batch_tune",
+           "ocp_batch_set_shape", "ocp_batch_get_shape", "ocp_batch_get_status", "ocp_grid_set_shape",
+           "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
 
 
 class OcpError(RuntimeError):
@@ -59,6 +62,15 @@ class _Desc(ctypes.Structure):
     _fields_ += [("nwell", ctypes.c_int), ("wells", ctypes.POINTER(_Well))]
 
 
+class _BatchIO(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("u_new", "flag_new", "u_old", "flag_old", "residual",
+                                                "bsr_val", "face_flux")]
+
+
+class _Shape(ctypes.Structure):
+    _fields_ = [("cells_per_tile", ctypes.c_int * 3), ("ctas_per_sm", ctypes.c_int * 3)]
+
+
 _lib = None
 
 
@@ -89,6 +101,16 @@ def load(build_if_missing: bool = False):
     lib.ocp_well_rates.argtypes = [vp, vp, vp, vp, vp]
     lib.ocp_get_status.argtypes = [vp, vp]
     lib.ocp_probe_fp64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.ocp_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+    lib.ocp_batch_destroy.argtypes = [vp]
+    lib.ocp_batch_set_io.argtypes = [vp, ctypes.POINTER(_BatchIO)]
+    lib.ocp_batch_linearize.argtypes = [vp, ctypes.c_double, vp]
+    lib.ocp_batch_graph_launch.argtypes = [vp, ctypes.c_double, vp]
+    lib.ocp_batch_tune.argtypes = [vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_Shape), vp]
+    lib.ocp_batch_set_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
+    lib.ocp_batch_get_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
+    lib.ocp_batch_get_status.argtypes = [vp, vp]
+    lib.ocp_grid_set_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
     lib.ocp_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "ocp_last_error":
@@ -281,6 +303,83 @@ class Grid:
     def status(self, stream=None):
         """Synchronise and return the sticky device status (an int, 0 = OK)."""
         return load().ocp_get_status(self._h, _stream(self.device, stream))
+
+    def set_shape(self, d):
+        """Launch shape of ocp_linearize on this grid (``ocp_grid_set_shape``)."""
+        _check(load().ocp_grid_set_shape(self._h, ctypes.byref(shape_from_dict(d))))
+
+
+def shape_to_dict(sh):
+    return {"cells_per_tile": list(sh.cells_per_tile), "ctas_per_sm": list(sh.ctas_per_sm)}
+
+
+def shape_from_dict(d):
+    sh = _Shape()
+    for q in range(3):
+        sh.cells_per_tile[q] = int(d["cells_per_tile"][q])
+        sh.ctas_per_sm[q] = int(d["ctas_per_sm"][q])
+    return sh
+
+
+class Batch:
+    """An ensemble of grids linearised together (``ocp_batch_*``)."""
+
+    def __init__(self, grids):
+        lib = load()
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g._h.value for g in self.grids])
+        h = ctypes.c_void_p()
+        _check(lib.ocp_batch_create(arr, len(self.grids), ctypes.byref(h)))
+        self._h = h
+        self.device = self.grids[0].device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ocp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_io(self, ios):
+        """ios: one dict per grid with u_new, flag_new, u_old, flag_old,
+        residual, bsr_val[, face_flux] device tensors."""
+        arr = (_BatchIO * len(self.grids))()
+        self._io = ios
+        for k, (g, io) in enumerate(zip(self.grids, ios)):
+            nb, N = g.nb, g.N
+            g._t(io["u_new"], nb * N, torch.float64, "u_new")
+            g._t(io["u_old"], nb * N, torch.float64, "u_old")
+            g._t(io["residual"], nb * N, torch.float64, "residual")
+            g._t(io["bsr_val"], g.nnzb * nb * nb, torch.float64, "bsr_val")
+            g._t(io.get("face_flux"), 3 * nb * N, torch.float64, "face_flux", allow_none=True)
+            for name in _BatchIO._fields_:
+                t = io.get(name[0])
+                setattr(arr[k], name[0], t.data_ptr() if t is not None else None)
+        _check(load().ocp_batch_set_io(self._h, arr))
+
+    def linearize(self, dt, graph=False, stream=None):
+        f = load().ocp_batch_graph_launch if graph else load().ocp_batch_linearize
+        _check(f(self._h, float(dt), _stream(self.device, stream)))
+
+    def tune(self, dt, reps=3, stream=None):
+        sh = _Shape()
+        _check(load().ocp_batch_tune(self._h, float(dt), int(reps), ctypes.byref(sh), _stream(self.device, stream)))
+        return shape_to_dict(sh)
+
+    def set_shape(self, d):
+        _check(load().ocp_batch_set_shape(self._h, ctypes.byref(shape_from_dict(d))))
+
+    def get_shape(self):
+        sh = _Shape()
+        _check(load().ocp_batch_get_shape(self._h, ctypes.byref(sh)))
+        return shape_to_dict(sh)
+
+    def status(self, stream=None):
+        return load().ocp_batch_get_status(self._h, _stream(self.device, stream))
 
 
 def probe_fp64(device=0, reps=3):
