@@ -243,6 +243,51 @@ ocp_status ocp_batch_get_status(ocp_batch* batch, void* cuda_stream);
  * ocp_batch_tune on a batch of that grid alone). */
 ocp_status ocp_grid_set_shape(ocp_grid* grid, const ocp_launch_shape* shape);
 
+/* ---------------------------------------------------------------- Newton step
+ * The rest of the FIM nonlinear iteration of Sec. 3.2.5 -- the linear solve
+ * and update of step 2, the convergence data of step 4 -- and what the
+ * multi-step adjoint needs around ocp_adjoint_vjp. */
+
+/* Device workspace (doubles) that ocp_bicgstab needs for this grid. */
+int64_t ocp_solver_work_doubles(const ocp_grid* grid);
+
+/* Solves A x = b (A^T x = b with transpose != 0) for the grid's block-CSR
+ * matrix bsr_val by BiCGSTAB with a block-Jacobi preconditioner D (exact
+ * inverses of the diagonal blocks, left preconditioning) until
+ * ||D^-1 (b - A x)|| <= rtol ||D^-1 b|| or maxit iterations -- a residual
+ * scaled cell by cell into the units of the unknowns.  x holds the initial guess
+ * on entry and the solution on return; b and x are block-interleaved [nb*N]
+ * device vectors; work is a device buffer of ocp_solver_work_doubles().
+ * Synchronises the stream once per iteration (to test convergence).  The
+ * paper solves with CPR-preconditioned FGMRES in PETSc/Hypre (Sec. 5.1); this
+ * plain Krylov solver serves the adjoint and test drivers.  Returns
+ * OCP_ERR_TIMEOUT when maxit is reached, OCP_ERR_NONFINITE on breakdown;
+ * *iters and *relres (may be NULL) report the final state. */
+ocp_status ocp_bicgstab(ocp_grid* grid, const double* bsr_val, const double* b, double* x, double rtol,
+                        int maxit, int transpose, double* work, int* iters, double* relres, void* cuda_stream);
+
+/* Newton update u += scale * du (du block-interleaved, u and flag as for
+ * ocp_linearize; scale = -1 applies the solution of J x = R), with every
+ * cell's saturation changes scaled down to at most
+ * ds_max, then the phase switch of undersaturated oil: a saturated cell whose
+ * S_g falls below zero becomes undersaturated with X = R_s,sat(p); an
+ * undersaturated cell whose R_s exceeds R_s,sat(p) becomes saturated with
+ * S_g = 0.  Writes the largest |du| applied per variable to du_max (device,
+ * nb + 1 doubles: p, S_w, S_g, R_s) and the number of switched cells to
+ * *nswitch (device int). */
+ocp_status ocp_newton_update(ocp_grid* grid, double* u, int8_t* flag, const double* du, double scale,
+                             double ds_max, double* du_max, int* nswitch, void* cuda_stream);
+
+/* Adjoint of ocp_well_rates: for device cotangents q_bar[nwell*nb], ADDS
+ * sum q_bar dq/du into g_u (variable-major like u; may be NULL) and
+ * sum q_bar dq/d ln k into g_lnk[N] (may be NULL). */
+ocp_status ocp_well_rates_vjp(ocp_grid* grid, const double* u, const int8_t* flag, const double* q_bar,
+                              double* g_u, double* g_lnk, void* cuda_stream);
+
+/* Recomputes the transmissibilities, their ln k weights and the well indices
+ * from a new permeability field lnk[N] (device), as ocp_grid_create did. */
+ocp_status ocp_grid_update_perm(ocp_grid* grid, const double* lnk, void* cuda_stream);
+
 /* Synchronises the stream, then returns and clears the grid's sticky device
  * status (OCP_OK if no kernel reported a problem since the last call). */
 ocp_status ocp_get_status(ocp_grid* grid, void* cuda_stream);

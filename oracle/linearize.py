@@ -233,9 +233,12 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
 
     # ---- wells (AllWells): bottom-hole-pressure controlled perforations
     well_q = np.zeros((N, nb))
-    for w in spec.wells:
+    well_rate = np.zeros((len(spec.wells), nb))
+    well_grad = []          # per well: (cells, dq/dlocal of shape (nperf, nb, L))
+    for iw, w in enumerate(spec.wells):
         cells_w = np.asarray(w.cells, dtype=np.int64)
         if len(cells_w) == 0:
+            well_grad.append((cells_w, np.zeros((0, nb, L))))
             continue
         P = {key: val_.take(cells_w) for key, val_ in pn.items() if val_ is not None}
         WI = well_index(spec, w, lnk.take(cells_w))
@@ -255,8 +258,10 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
             b_inj = P["b_w"] if w.phase == 0 else P["b_g"]
             q_inj = where(open_, WI * mob * b_inj * drive, zero)
             qs = [zero if e != (0 if w.phase == 0 else 2) else q_inj for e in range(nb)]
+        well_grad.append((cells_w, np.stack([qs[e].g for e in range(nb)], axis=1)))
         for e in range(nb):
             q = qs[e]
+            well_rate[iw, e] = q.v.sum()
             well_q[cells_w, e] += q.v
             add_rows(cells_w, e, q, -1.0)
             add_block(diag[cells_w], e, q.g[:, :nv], q.gm[:, :nv], -1.0)
@@ -267,7 +272,8 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
     out = {
         "R": R, "R_mag": Rm, "row_ptr": row_ptr, "col_idx": col_idx,
         "val": val, "val_mag": valm, "acc": np.stack([a.v for a in acc], axis=1),
-        "well_q": well_q, "face_flux": face_flux, "face_flux_mag": face_flux_mag,
+        "well_q": well_q, "well_rate": well_rate, "well_grad": well_grad,
+        "face_flux": face_flux, "face_flux_mag": face_flux_mag,
         "face_dphi": face_dphi,
     }
     if gw is not None:

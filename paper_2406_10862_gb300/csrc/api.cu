@@ -167,7 +167,8 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
       p.well = w;
       p.kind = W.kind;
       p.phase = W.phase;
-      p.wi = std::exp(d->lnk[c]) * geom;
+      p.geom = geom;
+      p.wi = 0.0;   // k * geom, filled on the device below
       p.p_bh = W.p_bh;
       perf.push_back(p);
     }
@@ -234,6 +235,9 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
     g->cfg.ctas_per_sm[s] = 0;
   }
   g->sms = 0;
+  g->dx = d->dx;
+  g->dy = d->dy;
+  g->kz_over_kx = d->kz_over_kx;
   g->nnzb = 7 * N - 2 * ((long long)d->ny * d->nz + (long long)d->nx * d->nz + (long long)d->nx * d->ny);
   g->scratch_doubles = ocp::linearize_scratch_doubles(N);
 
@@ -266,6 +270,7 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
     e = cudaMemcpy(g->d_well_first, well_first.data(), sizeof(int32_t) * well_first.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = ocp::launch_setup(g, d_lnk, d->dx, d->dy, d->dz, d->kz_over_kx, 0);
+  if (e == cudaSuccess) e = ocp::launch_perf_wi(g, d_lnk, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(d_lnk);
   if (e != cudaSuccess) {

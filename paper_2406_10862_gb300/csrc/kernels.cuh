@@ -14,6 +14,8 @@ cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const d
                                      const int8_t* f_new, const double* u_old, const int8_t* f_old, double dt,
                                      double* res, double* val, double* face_flux, cudaStream_t s);
 ocp_status report(ocp_status st, const char* fmt, ...);
+cudaError_t launch_perf_wi(ocp_grid* g, const double* lnk, cudaStream_t s);
+int64_t solver_work_doubles(const ocp_grid* g);
 cudaError_t launch_tiles(int nb, const TileList* lists, const ModelArgs& single, const LaunchCfg& cfg,
                          int sms, cudaStream_t s);
 ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,

@@ -1,0 +1,421 @@
+// Newton-step support: the parts of the FIM nonlinear iteration (Sec. 3.2.5,
+// steps 2 and 4) around the linearisation -- a block-Jacobi preconditioned
+// BiCGSTAB solve on the block-CSR Jacobian (the paper hands this to CPR
+// solvers in PETSc/Hypre, Sec. 5.1; here it is a plain GPU Krylov method),
+// the update of the primary variables with a saturation chop and the
+// saturated/undersaturated phase switch, the adjoint of the well rates, and
+// the update of transmissibilities and well indices from a new ln k.
+//
+// The BiCGSTAB scalars never leave the device: every reduction ends in a
+// device scalar that the next kernels read, and the host only reads the
+// residual norm to decide when to stop.  Dot products are two-pass with a
+// fixed grid, so results are deterministic.
+#include <cmath>
+#include <vector>
+
+#include "kernels.cuh"
+#include "ocp_internal.cuh"
+
+namespace ocp {
+namespace {
+
+constexpr int kRedBlocks = 304;       // fixed partial-sum grid (2 per SM)
+constexpr int kRedThreads = 256;
+
+// scalar slots of the solver
+enum { S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_R0V, S_TS, S_TT, S_RR, S_BB, S_FLAG, S_TMP, S_COUNT };
+
+__global__ void __launch_bounds__(kRedThreads) dot_partial(long long n, const double* __restrict__ a,
+                                                            const double* __restrict__ b,
+                                                            double* __restrict__ part) {
+  __shared__ double sh[kRedThreads];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads)
+    s = fma(a[i], b[i], s);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kRedThreads) dot_final(const double* __restrict__ part, double* out) {
+  __shared__ double sh[kRedThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// BiCGSTAB scalar steps (one thread).  S_FLAG records a breakdown.
+__global__ void scal_beta(double* sc) {
+  const double rho = sc[S_RHO];
+  if (sc[S_RHO_OLD] == 0.0 || sc[S_OMEGA] == 0.0) { sc[S_FLAG] = 1.0; sc[S_BETA] = 0.0; return; }
+  sc[S_BETA] = (rho / sc[S_RHO_OLD]) * (sc[S_ALPHA] / sc[S_OMEGA]);
+}
+__global__ void scal_alpha(double* sc) {
+  if (sc[S_R0V] == 0.0) { sc[S_FLAG] = 1.0; sc[S_ALPHA] = 0.0; return; }
+  sc[S_ALPHA] = sc[S_RHO] / sc[S_R0V];
+}
+__global__ void scal_omega(double* sc) {
+  if (sc[S_TT] == 0.0) { sc[S_OMEGA] = 0.0; return; }   // s == 0: x is already exact
+  sc[S_OMEGA] = sc[S_TS] / sc[S_TT];
+  sc[S_RHO_OLD] = sc[S_RHO];
+}
+__global__ void scal_init(double* sc) {
+  sc[S_RHO_OLD] = 1.0; sc[S_ALPHA] = 1.0; sc[S_OMEGA] = 1.0; sc[S_FLAG] = 0.0; sc[S_BETA] = 0.0;
+}
+
+// p = r + beta (p - omega v)
+__global__ void upd_p(long long n, const double* __restrict__ r, double* __restrict__ p,
+                      const double* __restrict__ v, const double* __restrict__ sc) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  p[i] = fma(sc[S_BETA], fma(-sc[S_OMEGA], v[i], p[i]), r[i]);
+}
+// s = r - alpha v
+__global__ void upd_s(long long n, const double* __restrict__ r, const double* __restrict__ v,
+                      double* __restrict__ s, const double* __restrict__ sc) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  s[i] = fma(-sc[S_ALPHA], v[i], r[i]);
+}
+// x += alpha y + omega z;  r = s - omega t
+__global__ void upd_xr(long long n, double* __restrict__ x, const double* __restrict__ y,
+                       const double* __restrict__ z, double* __restrict__ r, const double* __restrict__ s,
+                       const double* __restrict__ t, const double* __restrict__ sc) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] = fma(sc[S_OMEGA], z[i], fma(sc[S_ALPHA], y[i], x[i]));
+  r[i] = fma(-sc[S_OMEGA], t[i], s[i]);
+}
+
+// Inverse of every diagonal block (of its transpose when TRANS).
+template <int NB>
+__global__ void block_jacobi_kernel(Params P, const int32_t* __restrict__ row_ptr, const double* __restrict__ val,
+                                    double* __restrict__ dinv, int trans, int* status) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.N) return;
+  const int i = (int)(c % P.nx), j = (int)((c / P.nx) % P.ny), k = (int)(c / P.nxy);
+  const int diag = (k > 0) + (j > 0) + (i > 0);
+  const double* D = val + ((long long)row_ptr[c] + diag) * NB * NB;
+  double a[NB][NB], inv[NB][NB];
+  for (int e = 0; e < NB; ++e)
+    for (int v = 0; v < NB; ++v) a[e][v] = trans ? D[v * NB + e] : D[e * NB + v];
+  double det;
+  if (NB == 3) {
+    const double c00 = a[1][1] * a[2][2] - a[1][2] * a[2][1];
+    const double c01 = a[1][2] * a[2][0] - a[1][0] * a[2][2];
+    const double c02 = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+    det = a[0][0] * c00 + a[0][1] * c01 + a[0][2] * c02;
+    const double id = 1.0 / det;
+    inv[0][0] = c00 * id;
+    inv[1][0] = c01 * id;
+    inv[2][0] = c02 * id;
+    inv[0][1] = (a[0][2] * a[2][1] - a[0][1] * a[2][2]) * id;
+    inv[1][1] = (a[0][0] * a[2][2] - a[0][2] * a[2][0]) * id;
+    inv[2][1] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) * id;
+    inv[0][2] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) * id;
+    inv[1][2] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) * id;
+    inv[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) * id;
+  } else {
+    det = a[0][0] * a[1][1] - a[0][1] * a[1][0];
+    const double id = 1.0 / det;
+    inv[0][0] = a[1][1] * id;
+    inv[0][1] = -a[0][1] * id;
+    inv[1][0] = -a[1][0] * id;
+    inv[1][1] = a[0][0] * id;
+  }
+  if (!(det != 0.0) || !finite(det)) atomicOr(status, kStatNonFinite);
+  for (int e = 0; e < NB; ++e)
+    for (int v = 0; v < NB; ++v) dinv[c * NB * NB + e * NB + v] = inv[e][v];
+}
+
+template <int NB>
+__global__ void bj_apply_kernel(long long N, const double* __restrict__ dinv, const double* __restrict__ x,
+                                double* __restrict__ y) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  double xv[NB];
+  for (int v = 0; v < NB; ++v) xv[v] = x[c * NB + v];
+  for (int e = 0; e < NB; ++e) {
+    double s = 0.0;
+    for (int v = 0; v < NB; ++v) s = fma(dinv[c * NB * NB + e * NB + v], xv[v], s);
+    y[c * NB + e] = s;
+  }
+}
+
+// Newton update with a per-cell saturation chop and the phase switch; also
+// the largest change of each variable (atomicMax on the bits of |du| >= 0,
+// which is exact and order-independent).
+template <int NB>
+__global__ void newton_update_kernel(Params P, const Table* __restrict__ gT, double* __restrict__ u,
+                                     int8_t* __restrict__ flag, const double* __restrict__ du, double scale,
+                                     double ds_max, unsigned long long* __restrict__ dmax,
+                                     int* __restrict__ nswitch) {
+  const long long N = P.N;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const Table& T = *gT;
+  double d[3] = {scale * du[c * NB], scale * du[c * NB + 1], NB == 3 ? scale * du[c * NB + 2] : 0.0};
+  const int f = (NB == 3) ? flag[c] : 0;
+  // saturation chop: scale the cell's saturation changes to at most ds_max
+  double big = fabs(d[1]);
+  if (NB == 3 && f == 0) big = fmax(big, fabs(d[2]));
+  if (big > ds_max) {
+    const double sc = ds_max / big;
+    d[1] *= sc;
+    if (NB == 3 && f == 0) d[2] *= sc;
+  }
+  atomicMax(&dmax[0], (unsigned long long)__double_as_longlong(fabs(d[0])));
+  atomicMax(&dmax[1], (unsigned long long)__double_as_longlong(fabs(d[1])));
+  if (NB == 3) atomicMax(&dmax[2 + f], (unsigned long long)__double_as_longlong(fabs(d[2])));
+  const double p = u[c] + d[0];
+  u[c] = p;
+  u[N + c] += d[1];
+  if (NB == 3) {
+    double x = u[2 * N + c] + d[2];
+    // saturated R_s at the new pressure, from the table piece containing p
+    const int kp = segment(T.pkey, T.nrow, dkey(p));
+    const double rs_sat = fma(p - T.p[kp], T.s[4][kp], T.y[4][kp]);
+    int nf = f;
+    if (f == 0 && x < 0.0) {            // free gas disappeared: undersaturated at the bubble point
+      nf = 1;
+      x = rs_sat;
+    } else if (f == 1 && x > rs_sat) {  // more gas than the oil can hold: free gas appears
+      nf = 0;
+      x = 0.0;
+    }
+    u[2 * N + c] = x;
+    if (nf != f) {
+      flag[c] = (int8_t)nf;
+      atomicAdd(nswitch, 1);
+    }
+  }
+}
+
+// Adjoint of the well rates: for the rate cotangents q_bar[w*nb + e],
+// g_u[v*N + c] += sum_e q_bar * dq/du and g_lnk[c] += sum_e q_bar * q
+// (the well index is proportional to k of the cell).
+template <int NB>
+__global__ void well_vjp_kernel(Params P, const Table* __restrict__ gT, const double* __restrict__ u,
+                                const int8_t* __restrict__ flag, const double* __restrict__ phi,
+                                const Perf* __restrict__ perf, int nperf, const double* __restrict__ qbar,
+                                double* __restrict__ g_u, double* __restrict__ g_lnk) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nperf) return;
+  const long long N = P.N;
+  const Perf w = perf[k];
+  const long long c = w.cell;
+  CellQ q{};
+  CellAux a{};
+  cell_quantities<NB, true>(P, *gT, u[c], u[N + c], (NB == 3) ? u[2 * N + c] : 0.0,
+                            (NB == 3) ? (flag[c] & 1) : 0, phi[c], q, a, w.kind == 1);
+  double src[3], ds[3][3];
+  well_source<NB>(w, q, a, src, ds);
+  double gl = 0.0;
+  for (int v = 0; v < NB; ++v) {
+    double s = 0.0;
+    for (int e = 0; e < NB; ++e) s = fma(qbar[w.well * NB + e], ds[e][v], s);
+    if (g_u) g_u[v * N + c] += s;
+  }
+  for (int e = 0; e < NB; ++e) gl = fma(qbar[w.well * NB + e], src[e], gl);
+  if (g_lnk) g_lnk[c] += gl;
+}
+
+__global__ void perf_wi_kernel(Perf* perf, int nperf, const double* __restrict__ lnk) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nperf) return;
+  perf[k].wi = exp(lnk[perf[k].cell]) * perf[k].geom;
+}
+
+unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_perf_wi(ocp_grid* g, const double* lnk, cudaStream_t s) {
+  if (g->nperf == 0) return cudaSuccess;
+  perf_wi_kernel<<<nblk(g->nperf, 64), 64, 0, s>>>(g->d_perf, g->nperf, lnk);
+  return cudaGetLastError();
+}
+
+int64_t solver_work_doubles(const ocp_grid* g) {
+  const int64_t n = (int64_t)g->prm.nb * g->prm.N;
+  return 8 * n + (int64_t)g->prm.nb * g->prm.nb * g->prm.N + kRedBlocks + S_COUNT + 8;
+}
+
+}  // namespace ocp
+
+namespace {
+
+struct Guard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit Guard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+  }
+  ~Guard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int64_t ocp_solver_work_doubles(const ocp_grid* g) { return g ? ocp::solver_work_doubles(g) : 0; }
+
+ocp_status ocp_bicgstab(ocp_grid* g, const double* val, const double* b, double* x, double rtol, int maxit,
+                        int transpose, double* work, int* iters, double* relres, void* stream) {
+  using namespace ocp;
+  if (!g || !val || !b || !x || !work) return report(OCP_ERR_INVALID_ARG, "grid, val, b, x and work are required");
+  if (!(rtol > 0.0) || maxit < 1) return report(OCP_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 1");
+  if (b == x) return report(OCP_ERR_INVALID_ARG, "b and x must not overlap");
+  Guard guard(g->device);
+  if (guard.err != cudaSuccess) return report(OCP_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(guard.err));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = g->prm.nb;
+  const long long N = g->prm.N, n = nb * N;
+  double* r = work;
+  double* r0 = r + n;
+  double* p = r0 + n;
+  double* v = p + n;
+  double* sv = v + n;
+  double* t = sv + n;
+  double* y = t + n;
+  double* z = y + n;
+  double* dinv = z + n;
+  double* part = dinv + (long long)nb * nb * N;
+  double* sc = part + kRedBlocks;
+  const unsigned bn = nblk(n), bc = nblk(N);
+  auto dot = [&](const double* a, const double* c, int slot) {
+    dot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, a, c, part);
+    dot_final<<<1, kRedThreads, 0, s>>>(part, sc + slot);
+  };
+  auto apply = [&](const double* in, double* out) {
+    if (nb == 3) bj_apply_kernel<3><<<bc, 256, 0, s>>>(N, dinv, in, out);
+    else bj_apply_kernel<2><<<bc, 256, 0, s>>>(N, dinv, in, out);
+  };
+  cudaError_t e = cudaSuccess;
+  if (nb == 3) block_jacobi_kernel<3><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status);
+  else block_jacobi_kernel<2><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status);
+  // Left block-Jacobi preconditioning: BiCGSTAB on D^-1 A x = D^-1 b, so the
+  // residual that is tested is scaled cell by cell into the units of the
+  // unknowns (psi, saturation, scf/stb) and no equation dominates its norm.
+  // y = D^-1 b and r = D^-1 (b - A x)
+  apply(b, y);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = launch_spmv(g, val, -1.0, x, 1.0, t, transpose, s);
+  apply(t, r);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r0, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * n, s);
+  scal_init<<<1, 1, 0, s>>>(sc);
+  dot(y, y, S_BB);
+  dot(r, r, S_RR);
+  double h[S_COUNT];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab: %s", cudaGetErrorString(e));
+  const double bnorm = std::sqrt(h[S_BB]);
+  double res = std::sqrt(h[S_RR]);
+  int it = 0;
+  const double target = rtol * (bnorm > 0.0 ? bnorm : 1.0);
+  while (res > target && it < maxit) {
+    ++it;
+    dot(r0, r, S_RHO);
+    scal_beta<<<1, 1, 0, s>>>(sc);
+    upd_p<<<bn, 256, 0, s>>>(n, r, p, v, sc);
+    // v = D^-1 A p
+    e = launch_spmv(g, val, 1.0, p, 0.0, z, transpose, s);
+    apply(z, v);
+    dot(r0, v, S_R0V);
+    scal_alpha<<<1, 1, 0, s>>>(sc);
+    upd_s<<<bn, 256, 0, s>>>(n, r, v, sv, sc);
+    // t = D^-1 A s
+    if (e == cudaSuccess) e = launch_spmv(g, val, 1.0, sv, 0.0, z, transpose, s);
+    apply(z, t);
+    dot(t, sv, S_TS);
+    dot(t, t, S_TT);
+    scal_omega<<<1, 1, 0, s>>>(sc);
+    // x += alpha p + omega s;  r = s - omega t
+    upd_xr<<<bn, 256, 0, s>>>(n, x, p, sv, r, sv, t, sc);
+    dot(r, r, S_RR);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab: %s", cudaGetErrorString(e));
+    res = std::sqrt(h[S_RR]);
+    if (h[S_FLAG] != 0.0 || !std::isfinite(res)) break;
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = bnorm > 0.0 ? res / bnorm : res;
+  if (!std::isfinite(res)) return report(OCP_ERR_NONFINITE, "ocp_bicgstab: non-finite residual");
+  if (res > target) return report(OCP_ERR_TIMEOUT, "ocp_bicgstab: no convergence in %d iterations (relres %.3e)",
+                                  it, bnorm > 0.0 ? res / bnorm : res);
+  return OCP_OK;
+}
+
+ocp_status ocp_newton_update(ocp_grid* g, double* u, int8_t* flag, const double* du, double scale,
+                             double ds_max, double* du_max, int* nswitch, void* stream) {
+  using namespace ocp;
+  if (!g || !u || !du || !du_max || !nswitch || (g->prm.nb == 3 && !flag))
+    return report(OCP_ERR_INVALID_ARG, "grid, u, flag, du, du_max and nswitch are required");
+  if (!(ds_max > 0.0)) return report(OCP_ERR_INVALID_ARG, "ds_max must be > 0");
+  Guard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = guard.err;
+  if (e == cudaSuccess) e = cudaMemsetAsync(du_max, 0, sizeof(double) * (g->prm.nb + 1), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(nswitch, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    unsigned long long* dm = reinterpret_cast<unsigned long long*>(du_max);
+    if (g->prm.nb == 3)
+      newton_update_kernel<3><<<nblk(g->prm.N), 256, 0, s>>>(g->prm, g->d_table, u, flag, du, scale, ds_max, dm, nswitch);
+    else
+      newton_update_kernel<2><<<nblk(g->prm.N), 256, 0, s>>>(g->prm, g->d_table, u, flag, du, scale, ds_max, dm, nswitch);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_newton_update: %s", cudaGetErrorString(e));
+  return OCP_OK;
+}
+
+ocp_status ocp_well_rates_vjp(ocp_grid* g, const double* u, const int8_t* flag, const double* q_bar,
+                              double* g_u, double* g_lnk, void* stream) {
+  using namespace ocp;
+  if (!g || !u || !q_bar || (g->prm.nb == 3 && !flag))
+    return report(OCP_ERR_INVALID_ARG, "grid, u, flag and q_bar are required");
+  if (g->nperf == 0) return OCP_OK;
+  Guard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->prm.nb == 3)
+    well_vjp_kernel<3><<<nblk(g->nperf, 64), 64, 0, s>>>(g->prm, g->d_table, u, flag, g->d_phi, g->d_perf, g->nperf,
+                                                         q_bar, g_u, g_lnk);
+  else
+    well_vjp_kernel<2><<<nblk(g->nperf, 64), 64, 0, s>>>(g->prm, g->d_table, u, flag, g->d_phi, g->d_perf, g->nperf,
+                                                         q_bar, g_u, g_lnk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_well_rates_vjp: %s", cudaGetErrorString(e));
+  return OCP_OK;
+}
+
+ocp_status ocp_grid_update_perm(ocp_grid* g, const double* lnk, void* stream) {
+  using namespace ocp;
+  if (!g || !lnk) return report(OCP_ERR_INVALID_ARG, "grid and lnk are required");
+  Guard guard(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = guard.err;
+  if (e == cudaSuccess) e = launch_setup(g, lnk, g->dx, g->dy, g->prm.dz, g->kz_over_kx, s);
+  if (e == cudaSuccess) e = launch_perf_wi(g, lnk, s);
+  if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_grid_update_perm: %s", cudaGetErrorString(e));
+  return OCP_OK;
+}
+
+}  // extern "C"

@@ -68,6 +68,7 @@ struct Perf {
   int phase;      // injected phase (0 water, 2 gas)
   double wi;      // Peaceman index including k of the cell
   double p_bh;
+  double geom;    // C 2 pi dz / (ln(r_o / r_w) + skin): wi = k geom
 };
 
 // Launch shape of the three linearisation stages (cell, face, assemble):
@@ -102,6 +103,7 @@ struct ocp_grid {
   int64_t scratch_doubles;
   ocp::LaunchCfg cfg;        // launch shape of the linearisation
   int sms;                   // SM count of the device
+  double dx, dy, kz_over_kx; // geometry kept for permeability updates
 };
 
 namespace ocp {

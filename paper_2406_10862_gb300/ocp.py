@@ -29,7 +29,8 @@ EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_patt
            "ocp_linearize_noalloc", "ocp_probe_fp64", "ocp_batch_create", "ocp_batch_destroy",
            "ocp_batch_set_io", "ocp_batch_linearize", "ocp_batch_graph_launch", "ocp_batch_tune",
            "ocp_batch_set_shape", "ocp_batch_get_shape", "ocp_batch_get_status", "ocp_grid_set_shape",
-           "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
+           "ocp_solver_work_doubles", "ocp_bicgstab", "ocp_newton_update", "ocp_well_rates_vjp",
+           "ocp_grid_update_perm", "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
 
 
 class OcpError(RuntimeError):
@@ -111,9 +112,16 @@ def load(build_if_missing: bool = False):
     lib.ocp_batch_get_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
     lib.ocp_batch_get_status.argtypes = [vp, vp]
     lib.ocp_grid_set_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
+    lib.ocp_solver_work_doubles.argtypes = [vp]
+    lib.ocp_solver_work_doubles.restype = ctypes.c_int64
+    lib.ocp_bicgstab.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp,
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp]
+    lib.ocp_newton_update.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
+    lib.ocp_well_rates_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.ocp_grid_update_perm.argtypes = [vp, vp, vp]
     lib.ocp_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name != "ocp_last_error":
+        if name not in ("ocp_last_error", "ocp_solver_work_doubles"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -303,6 +311,34 @@ class Grid:
     def status(self, stream=None):
         """Synchronise and return the sticky device status (an int, 0 = OK)."""
         return load().ocp_get_status(self._h, _stream(self.device, stream))
+
+    # ------------------------------------------------------------ Newton support
+    def solver_work(self):
+        return self.empty(int(load().ocp_solver_work_doubles(self._h)))
+
+    def bicgstab(self, bsr_val, b, x, rtol, maxit, transpose=False, work=None, stream=None, check=True):
+        """Solve A x = b (A^T x = b); x is the initial guess, updated in place.
+        Returns (status, iterations, relative residual)."""
+        work = work if work is not None else self.solver_work()
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        st = load().ocp_bicgstab(self._h, _ptr(bsr_val), _ptr(b), _ptr(x), float(rtol), int(maxit),
+                                 int(bool(transpose)), _ptr(work), ctypes.byref(it), ctypes.byref(rr),
+                                 _stream(self.device, stream))
+        if check:
+            _check(st)
+        return st, it.value, rr.value
+
+    def newton_update(self, u, flag, du, scale, ds_max, du_max, nswitch, stream=None):
+        _check(load().ocp_newton_update(self._h, _ptr(u), _ptr(flag), _ptr(du), float(scale), float(ds_max),
+                                        _ptr(du_max), _ptr(nswitch), _stream(self.device, stream)))
+
+    def well_rates_vjp(self, u, flag, q_bar, g_u=None, g_lnk=None, stream=None):
+        _check(load().ocp_well_rates_vjp(self._h, _ptr(u), _ptr(flag), _ptr(q_bar), _ptr(g_u), _ptr(g_lnk),
+                                         _stream(self.device, stream)))
+
+    def update_perm(self, lnk, stream=None):
+        self._t(lnk, self.N, torch.float64, "lnk")
+        _check(load().ocp_grid_update_perm(self._h, _ptr(lnk), _stream(self.device, stream)))
 
     def set_shape(self, d):
         """Launch shape of ocp_linearize on this grid (``ocp_grid_set_shape``)."""

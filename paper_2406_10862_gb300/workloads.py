@@ -267,3 +267,24 @@ def tiny(nx, ny, nz, nphase=3, seed=0, frac_unsat=0.3, wells=True, **over):
             g.wells.append(Well(kind=1, phase=2 if nphase == 3 else 0, p_bh=5100.0,
                                 cells=g.column(0, 0)))
     return g, perturbed_state(g, rng, frac_unsat=frac_unsat if nphase == 3 else 0.0)
+
+
+def history_match(nx=100, ny=100, nz=10, seed_truth=51, seed_prior=52, seed_rock=5, nsteps=20, dt=1.0):
+    """History-matching case on a 100x100x10 three-phase box (100 000 cells):
+    a truth ln k and a prior ln k, both layered (per-layer means ~ U(ln 10,
+    ln 1000) mD plus N(0, 0.5) noise) from different seeds; porosity, wells
+    (four producers at 3500 psi, a gas injector at 5500 psi, all layers) and
+    the uniform initial state (p = 4800 psi, S_w = 0.12, S_g = 0) shared;
+    20 steps of 1 day.  Returns (grid with the prior ln k, initial state,
+    ln k truth, ln k prior, dt, number of steps)."""
+    g, _ = layered_box(seed=seed_rock, nx=nx, ny=ny, nz=nz)
+    lnk_truth = layered_lnk(np.random.default_rng(seed_truth), nx, ny, nz)
+    lnk_prior = layered_lnk(np.random.default_rng(seed_prior), nx, ny, nz)
+    g.lnk = np.ascontiguousarray(lnk_prior)
+    N = g.N
+    u0 = np.zeros((3, N))
+    u0[0] = 4800.0
+    u0[1] = 0.12
+    f0 = np.zeros(N, dtype=np.int8)
+    st = State(u_new=u0.copy(), flag_new=f0.copy(), u_old=u0, flag_old=f0, dt=dt)
+    return g, st, lnk_truth, lnk_prior, dt, nsteps

@@ -27,7 +27,7 @@ def declared():
     for f in os.listdir(inc):
         if f.endswith(".h"):
             src = open(os.path.join(inc, f)).read()
-            names |= set(re.findall(r"^\s*(?:ocp_status|const char\*|int|void)\s+(ocp_\w+)\s*\(", src, re.M))
+            names |= set(re.findall(r"^\s*(?:ocp_status|const char\*|int64_t|int|void)\s+(ocp_\w+)\s*\(", src, re.M))
     return names
 
 
