@@ -369,6 +369,10 @@ def run_gpu(args, rank, world, local_rank):
         }
         if not args.no_ensemble:
             line["ensemble"] = run_ensemble(dev, local_rank, reps=max(5, min(args.steps, 20)))
+        if not args.no_extra:
+            line["small_case"] = run_small_case(dev, local_rank)
+            line["oil_water"] = run_oil_water(dev, local_rank)
+            line["adjoint"] = run_adjoint(dev, local_rank)
         if world == 1 and not args.no_cpu_baseline:
             t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s)
             cpu = 1e-6 / cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp)
@@ -441,6 +445,151 @@ def run_ensemble(dev, local_rank, reps=10):
             "launches_batched": 3}
 
 
+def _events(stream):
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_small_case(dev, local_rank, reps=200):
+    """The 10x10x3 three-phase box (300 cells): launch-latency bound, so its
+    figure is microseconds per linearisation, as three stream launches and as
+    one CUDA-graph replay (a one-model batch)."""
+    import numpy as np
+    import torch
+
+    from paper_2406_10862_gb300 import ocp, workloads as W
+
+    g, s = W.spe1_like()
+    grid = ocp.Grid(g, local_rank)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    io = dict(u_new=T(s.u_new.ravel()), flag_new=T(s.flag_new), u_old=T(s.u_old.ravel()), flag_old=T(s.flag_old),
+              residual=torch.empty(3 * grid.N, dtype=torch.float64, device=dev),
+              bsr_val=torch.empty(grid.nnzb * 9, dtype=torch.float64, device=dev))
+    batch = ocp.Batch([grid])
+    batch.set_io([io])
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, fn in (("stream_us", lambda: grid.linearize(io["u_new"], io["flag_new"], io["u_old"], io["flag_old"],
+                                                           s.dt, io["residual"], io["bsr_val"])),
+                     ("graph_us", lambda: batch.linearize(s.dt, graph=True))):
+        for _ in range(20):
+            fn()
+        e0, e1 = _events(stream)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out[name] = e0.elapsed_time(e1) * 1e3 / reps
+    out.update(workload="10x10x3 three-phase box (300 cells)", cells=grid.N, status=batch.status())
+    return out
+
+
+def run_oil_water(dev, local_rank, steps=10):
+    """The 60x220x85 channelised oil-water model (1 122 000 cells, 2x2
+    blocks): 10 steps of linearise + one SpMV, each step's new state the
+    previous one plus a seeded perturbation."""
+    import numpy as np
+    import torch
+
+    from paper_2406_10862_gb300 import ocp, workloads as W
+
+    g, s = W.channelised_ow()
+    grid = ocp.Grid(g, local_rank)
+    N, nb = grid.N, grid.nb
+    rng = np.random.default_rng(33)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    states = []
+    u = s.u_old.copy()
+    for k in range(steps + 1):
+        states.append(T(u.ravel()))
+        u = u.copy()
+        u[0] += rng.normal(0.0, 5.0, N)
+        u[1] = np.clip(u[1] + rng.uniform(0.0, 0.01, N), 0.0, 1.0)
+    r = torch.empty(nb * N, dtype=torch.float64, device=dev)
+    v = torch.empty(grid.nnzb * nb * nb, dtype=torch.float64, device=dev)
+    x = T(rng.normal(size=nb * N))
+    y = torch.empty(nb * N, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        grid.linearize(states[1], None, states[0], None, 1.0, r, v)
+        grid.spmv(v, x, 1.0, 0.0, y)
+    lin, spm = [], []
+    flush = torch.empty(512 * 2 ** 20 // 8, dtype=torch.float64, device=dev)
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = _events(stream)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        grid.linearize(states[k + 1], None, states[k], None, 1.0, r, v)
+        e1.record(stream)
+        grid.spmv(v, x, 1.0, 0.0, y)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        lin.append(e0.elapsed_time(e1))
+        spm.append(e1.elapsed_time(e2))
+    st = grid.status()
+    ms = statistics.mean(a + b for a, b in zip(lin, spm))
+    nnzb = grid.nnzb
+    return {"workload": "channelised oil-water 60x220x85 (1122000 cells, 2x2 BSR)", "steps": steps,
+            "linearize_ms": statistics.mean(lin), "spmv_ms": statistics.mean(spm), "ms_per_step": ms,
+            "mcells_per_s": N / (ms * 1e-3) / 1e6,
+            "spmv_gflops": 2.0 * 4 * nnzb / (statistics.mean(spm) * 1e-3) / 1e9, "device_status": st}
+
+
+def run_adjoint(dev, local_rank):
+    """Gradient of the squared well-rate mismatch with respect to ln k over
+    20 FIM steps on the 100x100x10 box (observed rates from the truth field),
+    checkpoints every 5 steps: forward and reverse wall time, and the adjoint
+    VJP kernel alone on the final state."""
+    import numpy as np
+    import torch
+
+    from paper_2406_10862_gb300 import fim, ocp, workloads as W
+
+    g, s, lnk_truth, lnk_prior, dt, nsteps = W.history_match()
+    grid = ocp.Grid(g, local_rank)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    hm = fim.HistoryMatch(grid, T(s.u_old.ravel()), T(s.flag_old), dt, nsteps, checkpoint=5)
+    _, _, rates = hm.run(T(lnk_truth))
+    hm.q_obs = torch.stack(rates)
+    hm.q_scale = hm.q_obs.abs().amax(dim=(0, 1)) + 1e-30
+    lnk = T(lnk_prior).requires_grad_(True)
+    hm.stepper.newton_iters = hm.stepper.linear_iters = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    loss = fim.HistoryMatchLoss.apply(lnk, hm)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    # the VJP kernel alone, at the last step's state
+    st = hm.stepper
+    u1, f1 = T(s.u_old.ravel()).clone(), T(s.flag_old).clone()
+    u2, f2 = st.step(u1, f1, dt)
+    _, val, ff = st.linearize_at(u2, f2, u1, f1, dt)
+    lam = T(np.random.default_rng(5).normal(size=3 * grid.N))
+    out = {k: torch.empty(n, dtype=torch.float64, device=dev) for k, n in
+           (("unew", 3 * grid.N), ("uold", 3 * grid.N), ("lnk", grid.N), ("phi", grid.N))}
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        grid.adjoint_vjp(u2, f2, u1, f1, dt, val, ff, lam, out=out)
+    e0, e1 = _events(stream)
+    e0.record(stream)
+    for _ in range(20):
+        grid.adjoint_vjp(u2, f2, u1, f1, dt, val, ff, lam, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    vjp_ms = e0.elapsed_time(e1) / 20
+    vjp_bytes = grid.nnzb * 9 * 8 + 4 * grid.nnzb * 3 + 8 * grid.N * (3 + 9 + 6 + 6 + 1 + 8)
+    return {"workload": "history match 100x100x10 (100000 cells), 20 steps of 1 day, checkpoints every 5",
+            "loss": float(loss), "forward_s": t1 - t0, "gradient_s": t2 - t1,
+            "newton_iterations": st.newton_iters, "linear_iterations": st.linear_iters,
+            "grad_norm": float(lnk.grad.norm()), "vjp_ms": vjp_ms,
+            "vjp_gbs_algorithmic": vjp_bytes / (vjp_ms * 1e-3) / 1e9, "device_status": grid.status()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,6 +598,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-model batched-ensemble measurement")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 300-cell, oil-water and history-match measurements")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, no CPU baseline): the command profiled by ncu")
     args = ap.parse_args()
