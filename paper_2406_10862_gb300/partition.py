@@ -1,0 +1,92 @@
+"""Slab partition of one grid over ranks, with ghost layers (Sec. 3.4).
+
+Each rank owns a contiguous range of layers k0 <= k < k1 and builds a
+sub-grid that adds one ghost layer on each side that has a neighbour rank.
+Only the primary variables of the ghost layers are exchanged (point-to-point,
+``torch.distributed`` send/recv: NCCL between GPUs, gloo on the CPU); the
+ghost cells' properties are then recomputed locally by the linearisation, as
+the paper describes for its ghost cells.  The rows of the owned cells in the
+sub-grid's Jacobian have exactly the blocks, in the same order, as the same
+rows of the whole grid's Jacobian, and every row sums its terms in a fixed
+order, so the partitioned linearisation is bit-identical to the unpartitioned
+one.  Well perforations are kept on the rank that owns their cell.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+import torch.distributed as dist
+
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class Slab:
+    rank: int
+    world: int
+    k0: int            # first owned layer
+    k1: int            # one past the last owned layer
+    lo: int            # ghost layers below k0 (0 or 1)
+    hi: int            # ghost layers above k1 (0 or 1)
+    nxy: int
+
+    @property
+    def owned(self):
+        """Slice of the owned cells in the sub-grid's natural order."""
+        return slice(self.lo * self.nxy, (self.lo + self.k1 - self.k0) * self.nxy)
+
+    @property
+    def global_cells(self):
+        """Global natural index of every sub-grid cell."""
+        return np.arange((self.k0 - self.lo) * self.nxy, (self.k1 + self.hi) * self.nxy)
+
+
+def slab_of(nz, nxy, rank, world):
+    base, extra = divmod(nz, world)
+    k0 = rank * base + min(rank, extra)
+    k1 = k0 + base + (1 if rank < extra else 0)
+    return Slab(rank, world, k0, k1, 1 if k0 > 0 else 0, 1 if k1 < nz else 0, nxy)
+
+
+def subgrid(g: W.GridDesc, slab: Slab) -> W.GridDesc:
+    """The sub-grid of a slab: owned layers plus its ghost layers."""
+    cells = slab.global_cells
+    h = W.GridDesc(**{f: getattr(g, f) for f in g.__dataclass_fields__})
+    h.nz = slab.k1 - slab.k0 + slab.lo + slab.hi
+    h.top_depth = g.top_depth + (slab.k0 - slab.lo) * g.dz
+    h.lnk = np.ascontiguousarray(g.lnk[cells])
+    h.phi = np.ascontiguousarray(g.phi[cells])
+    first = slab.k0 * slab.nxy
+    last = slab.k1 * slab.nxy
+    h.wells = []
+    for w in g.wells:
+        mine = [int(c) - (slab.k0 - slab.lo) * slab.nxy for c in w.cells if first <= int(c) < last]
+        h.wells.append(W.Well(kind=w.kind, phase=w.phase, p_bh=w.p_bh, rw=w.rw, skin=w.skin,
+                              cells=np.array(mine, dtype=np.int64)))
+    return h
+
+
+def exchange_ghosts(u: torch.Tensor, slab: Slab, group=None):
+    """Fill the ghost layers of a variable-major sub-grid state u (nv, n_sub)
+    from the neighbour ranks' owned boundary layers (in place)."""
+    nxy, nl = slab.nxy, slab.k1 - slab.k0
+    reqs = []
+    lo_owned = u[:, slab.lo * nxy:(slab.lo + 1) * nxy].contiguous()
+    hi_owned = u[:, (slab.lo + nl - 1) * nxy:(slab.lo + nl) * nxy].contiguous()
+    lo_ghost = torch.empty_like(lo_owned)
+    hi_ghost = torch.empty_like(hi_owned)
+    if slab.lo:
+        reqs.append(dist.isend(lo_owned, slab.rank - 1, group=group))
+        reqs.append(dist.irecv(lo_ghost, slab.rank - 1, group=group))
+    if slab.hi:
+        reqs.append(dist.isend(hi_owned, slab.rank + 1, group=group))
+        reqs.append(dist.irecv(hi_ghost, slab.rank + 1, group=group))
+    for r in reqs:
+        r.wait()
+    if slab.lo:
+        u[:, :nxy] = lo_ghost
+    if slab.hi:
+        u[:, (slab.lo + nl) * nxy:] = hi_ghost
+    return u
