@@ -254,7 +254,8 @@ def run_gpu(args, rank, world, local_rank):
         if ev is not None:
             ev[3].record(stream)
 
-    fp64_peak = ocp.probe_fp64(local_rank, reps=3)   # attainable FP64 rate, measured now
+    # attainable FP64 rate, measured now (not under --profile, whose launch list is the workload's)
+    fp64_peak = None if args.profile else ocp.probe_fp64(local_rank, reps=3)
     for _ in range(args.warmup):
         flush.fill_(1.0)
         step()

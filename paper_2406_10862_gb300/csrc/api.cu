@@ -230,8 +230,11 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   P.bw_p_imu = (d->bw_ref * d->cw) * P.imu_w;
   P.vol_rb = d->dx * d->dy * d->dz / ocp::kRbFt3;
 
+  // default launch shape: 128-cell tiles for the register-heavy cell and
+  // face stages, 256 for assembly, one CTA per tile (ocp_grid_set_shape and
+  // the batch autotuner can change it)
   for (int s = 0; s < 3; ++s) {
-    g->cfg.tpb[s] = 256;
+    g->cfg.tpb[s] = s < 2 ? 128 : 256;
     g->cfg.ctas_per_sm[s] = 0;
   }
   g->sms = 0;

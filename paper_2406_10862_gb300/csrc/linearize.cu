@@ -134,7 +134,7 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c) {
   }
   const long long row0 = row_ptr[c];
   int slot = (int)hm[0] + (int)hm[1] + (int)hm[2] + 1;   // first + block of this row
-#pragma unroll
+#pragma unroll 1
   for (int d = 0; d < 3; ++d) {
     if (!hp[d]) {
       if (face_flux)
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) cell_kernel(TileList L, ModelA
 }
 
 template <int NB, int TPB>
-__global__ void __launch_bounds__(TPB) face_kernel(TileList L, ModelArgs single) {
+__global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) face_kernel(TileList L, ModelArgs single) {
   for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
     int m;
     long long c0;

@@ -133,11 +133,15 @@ __global__ void __launch_bounds__(256) spmv_kernel(long long N, const int32_t* _
 // Product on the grid's own pattern, one thread per block row.  The FP64
 // FMAs (NB*NB per block) are the binding resource on GB300, so the kernel
 // is arranged to keep them fed: the columns come from the 7-point structure
-// (no col_idx -> x dependent loads), all x entries of the row are loaded
-// first, then each block is loaded and consumed.  Rows with missing
-// neighbours read x at their own cell instead and skip those blocks.
+// and the row's first block from the closed form of the row pointer (no
+// dependent index loads), all x entries of the row are loaded first, then
+// each block is loaded and consumed.  Rows with missing neighbours read x
+// at their own cell instead and skip those blocks.  128-thread CTAs measured
+// fastest (28.4 us against 30.3 us with 256 at 200 000 rows).
+constexpr int kSpmvThreads = 128;
+
 template <int NB>
-__global__ void __launch_bounds__(256) spmv_grid_kernel(Params P, const int32_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const int32_t* __restrict__ row_ptr,
                                                         const double* __restrict__ val, double alpha,
                                                         const double* __restrict__ x, double beta,
                                                         double* __restrict__ y, int mode) {
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(256) spmv_grid_kernel(Params P, const int32_t*
 #pragma unroll
     for (int v = 0; v < NB; ++v) xv[t][v] = x[n * NB + v];
   }
-  const double* row = val + (long long)row_ptr[c] * B2;
+  const double* row = val + row_start(P, c) * B2;
   double acc[NB];
 #pragma unroll
   for (int e = 0; e < NB; ++e) acc[e] = 0.0;
@@ -339,12 +343,13 @@ cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, cons
   const long long N = g->prm.N;
   const unsigned blocks = (unsigned)((N + 255) / 256);
   const int mode = (beta != 0.0) ? 2 : (alpha != 1.0 ? 1 : 0);
+  const unsigned gblocks = (unsigned)((N + kSpmvThreads - 1) / kSpmvThreads);
   if (g->prm.nb == 3) {
     if (transpose) spmv_kernel<3, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
-    else spmv_grid_kernel<3><<<blocks, 256, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
+    else spmv_grid_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
   } else {
     if (transpose) spmv_kernel<2, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
-    else spmv_grid_kernel<2><<<blocks, 256, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
+    else spmv_grid_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
   }
   return cudaGetLastError();
 }
