@@ -210,6 +210,8 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   std::memset(&P, 0, sizeof(P));
   P.nx = d->nx; P.ny = d->ny; P.nz = d->nz; P.nb = nb;
   P.N = N; P.nxy = (long long)d->nx * d->ny;
+  ocp::div_magic((unsigned)d->nx, P.nx_m, P.nx_s);
+  ocp::div_magic((unsigned)d->ny, P.ny_m, P.ny_s);
   P.dz = d->dz;
   P.p_ref = d->p_ref; P.cr = d->cr; P.bw_ref = d->bw_ref; P.cw = d->cw; P.imu_w = 1.0 / d->muw;
   P.rho_osc = d->rho_osc; P.rho_wsc = d->rho_wsc; P.cg = d->rho_gsc / ocp::kRbFt3;

@@ -117,9 +117,8 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c) {
   double* __restrict__ val = M.val;
   double* __restrict__ face_flux = M.face_flux;
   const int32_t* __restrict__ row_ptr = M.row_ptr;
-  const int i = (int)(c % P.nx);
-  const int j = (int)((c / P.nx) % P.ny);
-  const int k = (int)(c / P.nxy);
+  int i, j, k;
+  cell_ijk(P, c, i, j, k);
   const bool hm[3] = {i > 0, j > 0, k > 0};
   const bool hp[3] = {i + 1 < P.nx, j + 1 < P.ny, k + 1 < P.nz};
   const long long stride[3] = {1, P.nx, P.nxy};
@@ -188,9 +187,8 @@ __device__ __forceinline__ void assemble_body(const ModelArgs& M, long long c) {
   const Params& P = M.P;
   const long long N = P.N;
   const double* __restrict__ scr = M.scr;
-  const int i = (int)(c % P.nx);
-  const int j = (int)((c / P.nx) % P.ny);
-  const int k = (int)(c / P.nxy);
+  int i, j, k;
+  cell_ijk(P, c, i, j, k);
   const bool hm[3] = {i > 0, j > 0, k > 0};
   double r[NB], dg[NB][NB];
 #pragma unroll

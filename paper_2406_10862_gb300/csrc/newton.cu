@@ -103,7 +103,8 @@ __global__ void block_jacobi_kernel(Params P, const int32_t* __restrict__ row_pt
                                     double* __restrict__ dinv, int trans, int* status) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= P.N) return;
-  const int i = (int)(c % P.nx), j = (int)((c / P.nx) % P.ny), k = (int)(c / P.nxy);
+  int i, j, k;
+  cell_ijk(P, c, i, j, k);
   const int diag = (k > 0) + (j > 0) + (i > 0);
   const double* D = val + ((long long)row_ptr[c] + diag) * NB * NB;
   double a[NB][NB], inv[NB][NB];

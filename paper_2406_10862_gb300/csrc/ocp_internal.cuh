@@ -55,6 +55,8 @@ struct Params {
   double pcow_max, pcgo_max;
   double grav_dz;                         // 0.5 * g * dz: half the potential head per unit density
   double vol_rb;                          // cell bulk volume in rb
+  unsigned long long nx_m, ny_m;          // exact division by nx and ny: q = (c * m) >> (32 + s)
+  int nx_s, ny_s;
   double pcow2, pcgo2;                    // 2 Pc_max (derivative factors)
   double bw_p;                            // d b_w / dp
   double rw_p, bw_p_imu;                  // d rho_w / dp, (d b_w / dp) / mu_w
@@ -141,6 +143,44 @@ struct TileList {
 }  // namespace ocp
 
 namespace ocp {
+
+// ------------------------------------------------------------ cell indices
+// Division of a non-negative 32-bit c by an invariant d as a multiply and a
+// shift (the round-up method: m = floor(2^(32+s)/d) + 1, s = ceil(log2 d),
+// exact for every 32-bit c).  Integer division is otherwise a long
+// instruction sequence with a reciprocal; the cell index is split in every
+// kernel, so this keeps the integer work off the FP64 kernels' critical path.
+__host__ __device__ inline void div_magic(unsigned d, unsigned long long& m, int& s) {
+  s = 0;
+  while ((1ull << s) < d) ++s;
+  m = ((1ull << (32 + s)) / d) + 1;
+}
+__device__ __forceinline__ int fdiv(int c, unsigned long long m, int s) {
+  return (int)(((unsigned long long)(unsigned)c * m) >> (32 + s));
+}
+// (i, j, k) of cell c
+__device__ __forceinline__ void cell_ijk(const Params& P, long long c, int& i, int& j, int& k) {
+  const int ci = (int)c;
+  const int q = fdiv(ci, P.nx_m, P.nx_s);
+  i = ci - q * P.nx;
+  k = fdiv(q, P.ny_m, P.ny_s);
+  j = q - k * P.ny;
+}
+// Number of stored blocks in the rows before cell c = (i, j, k): 7 per
+// earlier cell minus the missing neighbours of every earlier cell, in
+// closed form.
+__device__ __forceinline__ long long row_start_ijk(const Params& P, long long c, int i, int j, int k) {
+  const long long nx = P.nx, nxy = P.nxy, N = P.N;
+  const long long q = (long long)k * P.ny + j;            // c / nx
+  const long long i0 = q + (i > 0);                        // earlier cells with i == 0
+  const long long iL = q;                                  // ... with i == nx-1
+  const long long rem = (long long)j * nx + i;             // c % nxy
+  const long long j0 = k * nx + (rem < nx ? rem : nx);     // ... with j == 0
+  const long long jL = k * nx + (rem > nxy - nx ? rem - (nxy - nx) : 0);
+  const long long k0 = c < nxy ? c : nxy;                  // ... with k == 0
+  const long long kL = c > N - nxy ? c - (N - nxy) : 0;    // ... with k == nz-1
+  return 7 * c - (i0 + iL + j0 + jL + k0 + kL);
+}
 
 // ---------------------------------------------------------------- bit tricks
 // Order-preserving signed integer key of a double (total order on non-NaN).

@@ -24,25 +24,18 @@ namespace {
 // ------------------------------------------------------------------ pattern
 // Neighbour types in column order: -z, -y, -x, self, +x, +y, +z.
 __device__ __forceinline__ void neighbours(const Params& P, long long c, bool* has) {
-  const int i = (int)(c % P.nx);
-  const int j = (int)((c / P.nx) % P.ny);
-  const int k = (int)(c / P.nxy);
+  int i, j, k;
+  cell_ijk(P, c, i, j, k);
   has[0] = k > 0; has[1] = j > 0; has[2] = i > 0; has[3] = true;
   has[4] = i + 1 < P.nx; has[5] = j + 1 < P.ny; has[6] = k + 1 < P.nz;
 }
 
-// Number of stored blocks in the rows before c (closed form of the prefix
-// sum of 7 minus the missing neighbours of every earlier cell).
+// Number of stored blocks in the rows before c.
 __device__ __forceinline__ long long row_start(const Params& P, long long c) {
-  const long long nx = P.nx, nxy = P.nxy, N = P.N;
-  const long long i0 = (c + nx - 1) / nx;                 // earlier cells with i == 0
-  const long long iL = c / nx;                            // ... with i == nx-1
-  const long long lay = c / nxy, rem = c % nxy;
-  const long long j0 = lay * nx + (rem < nx ? rem : nx);  // ... with j == 0
-  const long long jL = lay * nx + (rem > nxy - nx ? rem - (nxy - nx) : 0);
-  const long long k0 = c < nxy ? c : nxy;                 // ... with k == 0
-  const long long kL = c > N - nxy ? c - (N - nxy) : 0;   // ... with k == nz-1
-  return 7 * c - (i0 + iL + j0 + jL + k0 + kL);
+  if (c >= P.N) return 7 * P.N - 2 * ((long long)P.ny * P.nz + (long long)P.nx * P.nz + P.nxy);
+  int i, j, k;
+  cell_ijk(P, c, i, j, k);
+  return row_start_ijk(P, c, i, j, k);
 }
 
 __global__ void setup_kernel(Params P, const double* __restrict__ lnk, double dx, double dy, double dz,
@@ -148,8 +141,9 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const
   constexpr int B2 = NB * NB;
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= P.N) return;
-  bool has[7];
-  neighbours(P, c, has);
+  int ci, cj, ck;
+  cell_ijk(P, c, ci, cj, ck);
+  const bool has[7] = {ck > 0, cj > 0, ci > 0, true, ci + 1 < P.nx, cj + 1 < P.ny, ck + 1 < P.nz};
   const long long off[7] = {-P.nxy, -P.nx, -1, 0, 1, P.nx, P.nxy};
   int slot[7];
   int s = 0;
@@ -165,7 +159,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const
 #pragma unroll
     for (int v = 0; v < NB; ++v) xv[t][v] = x[n * NB + v];
   }
-  const double* row = val + row_start(P, c) * B2;
+  const double* row = val + row_start_ijk(P, c, ci, cj, ck) * B2;
   double acc[NB];
 #pragma unroll
   for (int e = 0; e < NB; ++e) acc[e] = 0.0;
