@@ -288,6 +288,29 @@ ocp_status ocp_well_rates_vjp(ocp_grid* grid, const double* u, const int8_t* fla
  * from a new permeability field lnk[N] (device), as ocp_grid_create did. */
 ocp_status ocp_grid_update_perm(ocp_grid* grid, const double* lnk, void* cuda_stream);
 
+/* ---------------------------------------------------------------- adaptive coupling
+ * The adaptively coupled domain decomposition of Sec. 4 decides at the start
+ * of each time step which subdomains to solve together: (1) mark the cells
+ * whose phase saturation changed by more than `threshold` (the paper uses
+ * 5e-3) between (u_old, flag_old) and (u_new, flag_new); (2) couple a
+ * subdomain that holds a marked cell with every neighbouring subdomain, and a
+ * subdomain that sees a marked cell as a ghost with the subdomain owning it;
+ * (3) take the connected components of that graph.  Subdomains are the boxes
+ * of a px x py x pz split of the grid (box b along x holds the cells i with
+ * floor(i px / nx) == b, likewise along y and z).  labels[px*py*pz] (device)
+ * receives the smallest subdomain index of each subdomain's component; work
+ * is a device buffer of ocp_coupling_work_ints() ints; afterwards, with
+ * S = px py pz, work[2S] holds the number of marked cells, work[2S+1] the
+ * union-find retries and work[2S+2] an error flag (nonzero if a loop bound
+ * was reached, which the algorithm's invariants rule out).  Asynchronous on
+ * cuda_stream; labels and work are caller-owned; capturable in a CUDA graph.
+ * Returns OCP_ERR_INVALID_ARG for null pointers, px, py, pz outside
+ * [1, cells per direction] or a negative / non-finite threshold. */
+int64_t ocp_coupling_work_ints(int px, int py, int pz);
+ocp_status ocp_coupling_components(ocp_grid* grid, const double* u_new, const int8_t* flag_new,
+                                   const double* u_old, const int8_t* flag_old, double threshold, int px,
+                                   int py, int pz, int32_t* labels, int32_t* work, void* cuda_stream);
+
 /* Synchronises the stream, then returns and clears the grid's sticky device
  * status (OCP_OK if no kernel reported a problem since the last call). */
 ocp_status ocp_get_status(ocp_grid* grid, void* cuda_stream);

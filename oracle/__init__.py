@@ -14,7 +14,10 @@ Contents:
                  old state, ln k and porosity;
 * ``spmv``       block-CSR matrix-vector products written as plain loops;
 * ``newton``     a small Newton time stepper with a library sparse solve
-                 (used by the Buckley-Leverett pin and the gradient checks).
+                 (used by the Buckley-Leverett pin and the gradient checks);
+* ``adjoint``    multi-step simulation and its discrete-adjoint gradient;
+* ``coupling``   the adaptive subdomain coupling of Sec. 4 (marked cells,
+                 coupling graph, connected components).
 
 Parity status of each function is listed in the design notes; all of them are
 pinned by the CPU tests (``tests/test_oracle_*.py``).

@@ -30,7 +30,7 @@ EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_patt
            "ocp_batch_set_io", "ocp_batch_linearize", "ocp_batch_graph_launch", "ocp_batch_tune",
            "ocp_batch_set_shape", "ocp_batch_get_shape", "ocp_batch_get_status", "ocp_grid_set_shape",
            "ocp_solver_work_doubles", "ocp_bicgstab", "ocp_newton_update", "ocp_well_rates_vjp",
-           "ocp_grid_update_perm", "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
+           "ocp_grid_update_perm", "ocp_coupling_work_ints", "ocp_coupling_components", "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
 
 
 class OcpError(RuntimeError):
@@ -119,9 +119,13 @@ def load(build_if_missing: bool = False):
     lib.ocp_newton_update.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
     lib.ocp_well_rates_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.ocp_grid_update_perm.argtypes = [vp, vp, vp]
+    lib.ocp_coupling_work_ints.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.ocp_coupling_work_ints.restype = ctypes.c_int64
+    lib.ocp_coupling_components.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, vp, vp, vp]
     lib.ocp_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("ocp_last_error", "ocp_solver_work_doubles"):
+        if name not in ("ocp_last_error", "ocp_solver_work_doubles", "ocp_coupling_work_ints"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -339,6 +343,33 @@ class Grid:
     def update_perm(self, lnk, stream=None):
         self._t(lnk, self.N, torch.float64, "lnk")
         _check(load().ocp_grid_update_perm(self._h, _ptr(lnk), _stream(self.device, stream)))
+
+    def coupling_components(self, u_new, flag_new, u_old, flag_old, threshold, px, py, pz, labels=None,
+                            work=None, stream=None):
+        """``ocp_coupling_components``: adaptive coupling of the px x py x pz
+        subdomains (Sec. 4).  Returns (labels, work) device tensors: labels[s]
+        is the smallest subdomain index of s's component, work[2 S] the number
+        of marked cells, work[2 S + 1] the union-find retries and work[2 S + 2]
+        an error flag (1 if a loop bound was reached; never expected)."""
+        lib = load()
+        N, nb = self.N, self.nb
+        self._t(u_new, nb * N, torch.float64, "u_new")
+        self._t(u_old, nb * N, torch.float64, "u_old")
+        if nb == 3 or flag_new is not None:
+            self._t(flag_new, N, torch.int8, "flag_new")
+            self._t(flag_old, N, torch.int8, "flag_old")
+        S = int(px) * int(py) * int(pz)
+        nwork = int(lib.ocp_coupling_work_ints(int(px), int(py), int(pz)))
+        if S < 1 or nwork < 1:
+            raise ValueError("subdomain counts must be positive")
+        labels = labels if labels is not None else torch.empty(S, dtype=torch.int32, device=self.device)
+        work = work if work is not None else torch.empty(nwork, dtype=torch.int32, device=self.device)
+        self._t(labels, S, torch.int32, "labels")
+        self._t(work, nwork, torch.int32, "work")
+        _check(lib.ocp_coupling_components(self._h, _ptr(u_new), _ptr(flag_new), _ptr(u_old), _ptr(flag_old),
+                                           float(threshold), int(px), int(py), int(pz), _ptr(labels), _ptr(work),
+                                           _stream(self.device, stream)))
+        return labels, work
 
     def set_shape(self, d):
         """Launch shape of ocp_linearize on this grid (``ocp_grid_set_shape``)."""

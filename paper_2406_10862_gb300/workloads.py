@@ -288,3 +288,79 @@ def history_match(nx=100, ny=100, nz=10, seed_truth=51, seed_prior=52, seed_rock
     f0 = np.zeros(N, dtype=np.int8)
     st = State(u_new=u0.copy(), flag_new=f0.copy(), u_old=u0, flag_old=f0, dt=dt)
     return g, st, lnk_truth, lnk_prior, dt, nsteps
+
+
+# ----------------------------------------------------------------- moving fronts
+def front_state(g: GridDesc, seed, fronts, width=1.5, ds_front=0.02, ds_bg=2e-3, frac_unsat=0.2, dt=1.0):
+    """Pair of states whose saturations differ strongly only on thin moving
+    fronts, as around the injectors of a gas/water alternating flood.
+
+    ``fronts`` is a list of (ci, cj, ck, radius, phase) in cell units with
+    phase 0 (water) or 2 (gas): the cells whose centre lies within ``width``
+    of that sphere gain ``ds_front`` of that phase (gas only where the cell is
+    saturated).  Every other cell moves by less than ``ds_bg`` per phase; a
+    fraction ``frac_unsat`` of cells (three-phase) is undersaturated with X =
+    R_s rescaled by up to 3 %.  Some cells switch between saturated and
+    undersaturated over the step."""
+    rng = np.random.default_rng(seed)
+    N, nv = g.N, g.nphase
+    c = np.arange(N)
+    i, j, k = c % g.nx, (c // g.nx) % g.ny, c // (g.nx * g.ny)
+    u_old = np.zeros((nv, N))
+    u_old[0] = 4800.0 + rng.normal(0.0, 50.0, N)
+    u_old[1] = 0.12 + rng.uniform(0.0, 0.2, N)
+    f_old = np.zeros(N, dtype=np.int8)
+    if nv == 3:
+        u_old[2] = rng.uniform(0.0, 0.1, N)
+        unsat = rng.random(N) < frac_unsat
+        f_old[unsat] = 1
+        u_old[2, unsat] = rng.uniform(0.3, 0.9, int(unsat.sum())) * float(np.max(g.tab_Rs))
+    u_new = u_old.copy()
+    f_new = f_old.copy()
+    u_new[0] += rng.normal(0.0, 20.0, N)
+    u_new[1] += rng.uniform(-0.5, 0.5, N) * ds_bg
+    if nv == 3:
+        sat = f_old == 0
+        u_new[2, sat] = np.abs(u_new[2, sat] + rng.uniform(-0.5, 0.5, int(sat.sum())) * ds_bg)
+        u_new[2, ~sat] *= rng.uniform(0.97, 1.03, int((~sat).sum()))
+        # a few cells switch state, saturated -> undersaturated (only where
+        # little gas was present) and back
+        flip = rng.random(N) < 0.002
+        to_un = flip & sat & (u_old[2] < 0.5 * ds_bg)
+        to_sat = flip & ~sat
+        f_new[to_un] = 1
+        u_new[2, to_un] = 0.5 * float(np.max(g.tab_Rs))
+        f_new[to_sat] = 0
+        u_new[2, to_sat] = 0.0
+    for (ci, cj, ck, radius, phase) in fronts:
+        r = np.sqrt((i - ci) ** 2 + (j - cj) ** 2 + (k - ck) ** 2)
+        on = np.abs(r - radius) < width
+        if phase == 2 and nv == 3:
+            on &= f_new == 0
+            u_new[2, on] += ds_front
+        else:
+            u_new[1, on] += ds_front
+    return State(u_new=u_new, flag_new=f_new, u_old=u_old, flag_old=f_old, dt=dt)
+
+
+def addm_2d(seed=7, n=4000, radius_gas=None, radius_water=None):
+    """The two-dimensional flood used for the adaptive coupling: an n x n x 1
+    three-phase grid of 20 ft cells (n = 4000: 16 million cells), four
+    injectors at (n/4, n/4), (n/4, 3n/4), (3n/4, n/4), (3n/4, 3n/4) and nine
+    producers at the corners, edge midpoints and centre, ln k ~ N(ln 100, 1),
+    phi ~ U(0.15, 0.3).  The state pair has a gas front (radius n/8) and a
+    water front (radius n/16) around every injector."""
+    rng = np.random.default_rng(seed)
+    N = n * n
+    lnk = rng.normal(math.log(100.0), 1.0, N)
+    phi = rng.uniform(0.15, 0.3, N)
+    g = make_grid(n, n, 1, lnk, phi, [], dx=20.0, dy=20.0, dz=20.0)
+    q1, q3 = n // 4 - 1, (3 * n) // 4 - 1
+    inj = [(q1, q1), (q1, q3), (q3, q1), (q3, q3)]
+    edge = [0, n // 2 - 1, n - 1]
+    g.wells = [Well(kind=1, phase=2, p_bh=5500.0, cells=g.column(a, b)) for (a, b) in inj]
+    g.wells += [Well(kind=0, phase=0, p_bh=3500.0, cells=g.column(a, b)) for a in edge for b in edge]
+    rg = n / 8.0 if radius_gas is None else radius_gas
+    rw = n / 16.0 if radius_water is None else radius_water
+    fronts = [(a, b, 0, rg, 2) for (a, b) in inj] + [(a, b, 0, rw, 0) for (a, b) in inj]
+    return g, front_state(g, seed + 1, fronts)
