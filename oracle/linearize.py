@@ -114,13 +114,24 @@ def bsr_pattern(spec):
 
 
 # ----------------------------------------------------------------- linearise
-def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None):
+def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None, p_bh=None, controls=None):
     """Residual and Jacobian of one backward-Euler step.
 
     mode="unew": derivatives with respect to the new state only (the Jacobian).
     mode="all": per-cell local variables are (u_new[nv], u_old[nv], ln k, phi);
     with ``lam`` (N, nb) given, the vector-Jacobian products
     lam^T dR/d(u_new, u_old, ln k, phi) are returned too.
+
+    With ``p_bh`` (one value per well) the bottom-hole pressures are unknowns
+    too, and every well gets an equation (the "w" rows and columns of the
+    global Jacobian, Sec. 3.4.1): ``controls`` holds one (mode, phase, target)
+    per well -- mode 0 fixes the bottom-hole pressure, R_w = p_bh - target;
+    mode 1 fixes the surface rate of component ``phase``, R_w = s sum_perf
+    q_phase - target with s = -1 for producers (production counted positive)
+    and +1 for injectors.  Without ``controls`` every well is mode 0 at its own
+    p_bh.  The extra outputs are ``well_res`` (nwell), ``well_B`` (nperf, nb)
+    = dR_cell/dp_bh, ``well_C`` (nperf, nb) = dR_w/du_cell, ``well_D`` (nwell)
+    = dR_w/dp_bh, each with its magnitude scale, perforations in well order.
     """
     nx, ny, nz = dims(spec)
     N = nx * ny * nz
@@ -231,26 +242,46 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
                 np.add.at(gwm, fi, wm * q.gm[:, :L])
                 np.add.at(gwm, fj, wm * q.gm[:, L:])
 
-    # ---- wells (AllWells): bottom-hole-pressure controlled perforations
+    # ---- wells (AllWells): perforation sources at the bottom-hole pressure
+    nwell = len(spec.wells)
+    unknown_bhp = p_bh is not None
+    Lw = L + 1 if unknown_bhp else L      # slot L: the well's own p_bh
+    if unknown_bhp:
+        p_bh = np.asarray(p_bh, dtype=np.float64)
+        if controls is None:
+            controls = [(0, 0, float(w.p_bh)) for w in spec.wells]
+        w_res = np.zeros(nwell)
+        w_res_m = np.zeros(nwell)
+        w_D = np.zeros(nwell)
+        w_D_m = np.zeros(nwell)
+        w_B, w_B_m, w_C, w_C_m = [], [], [], []
     well_q = np.zeros((N, nb))
-    well_rate = np.zeros((len(spec.wells), nb))
+    well_rate = np.zeros((nwell, nb))
     well_grad = []          # per well: (cells, dq/dlocal of shape (nperf, nb, L))
     for iw, w in enumerate(spec.wells):
         cells_w = np.asarray(w.cells, dtype=np.int64)
-        if len(cells_w) == 0:
+        n_w = len(cells_w)
+        if n_w == 0:
             well_grad.append((cells_w, np.zeros((0, nb, L))))
+            if unknown_bhp:
+                mode, _, target = controls[iw]
+                w_res[iw] = (p_bh[iw] - target) if mode == 0 else -target
+                w_res_m[iw] = (abs(p_bh[iw]) + abs(target)) if mode == 0 else abs(target)
+                w_D[iw] = 1.0 if mode == 0 else 0.0
+                w_D_m[iw] = w_D[iw]
             continue
-        P = {key: val_.take(cells_w) for key, val_ in pn.items() if val_ is not None}
-        WI = well_index(spec, w, lnk.take(cells_w))
-        zero = D.const(0.0, len(cells_w), L)
+        P = {key: val_.take(cells_w).embed(Lw, 0) for key, val_ in pn.items() if val_ is not None}
+        WI = well_index(spec, w, lnk.take(cells_w)).embed(Lw, 0)
+        zero = D.const(0.0, n_w, Lw)
+        pw = D.seed(np.full(n_w, p_bh[iw]), Lw, L) if unknown_bhp else w.p_bh
         if w.kind == 0:  # producer: every mobile phase leaves where p > p_bh
-            drive = P["p_o"] - w.p_bh
+            drive = P["p_o"] - pw
             open_ = drive.v > 0.0
-            qs = [where(open_, WI * P["lam_" + a] * (w.p_bh - P["p_o"]), zero) for a in phases]
+            qs = [where(open_, WI * P["lam_" + a] * (pw - P["p_o"]), zero) for a in phases]
             if nb == 3:
                 qs[2] = qs[2] + P["Rs"] * qs[1]
         else:  # injector of one phase with the cell's total mobility
-            drive = w.p_bh - P["p_o"]
+            drive = pw - P["p_o"]
             open_ = drive.v > 0.0
             mob = P["kr_w"] * P["imu_w"] + P["kr_o"] * P["imu_o"]
             if nb == 3:
@@ -258,7 +289,7 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
             b_inj = P["b_w"] if w.phase == 0 else P["b_g"]
             q_inj = where(open_, WI * mob * b_inj * drive, zero)
             qs = [zero if e != (0 if w.phase == 0 else 2) else q_inj for e in range(nb)]
-        well_grad.append((cells_w, np.stack([qs[e].g for e in range(nb)], axis=1)))
+        well_grad.append((cells_w, np.stack([qs[e].g[:, :L] for e in range(nb)], axis=1)))
         for e in range(nb):
             q = qs[e]
             well_rate[iw, e] = q.v.sum()
@@ -266,8 +297,33 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
             add_rows(cells_w, e, q, -1.0)
             add_block(diag[cells_w], e, q.g[:, :nv], q.gm[:, :nv], -1.0)
             if gw is not None:
-                np.add.at(gw, cells_w, -lam[cells_w, e:e + 1] * q.g)
-                np.add.at(gwm, cells_w, alam[cells_w, e:e + 1] * q.gm)
+                np.add.at(gw, cells_w, -lam[cells_w, e:e + 1] * q.g[:, :L])
+                np.add.at(gwm, cells_w, alam[cells_w, e:e + 1] * q.gm[:, :L])
+        if unknown_bhp:
+            # the cell rows' dependence on p_bh (R_cell holds -q)
+            w_B.append(np.stack([-qs[e].g[:, L] for e in range(nb)], axis=1))
+            w_B_m.append(np.stack([qs[e].gm[:, L] for e in range(nb)], axis=1))
+            mode, ph, target = controls[iw]
+            if mode == 0:
+                w_res[iw] = p_bh[iw] - target
+                w_res_m[iw] = abs(p_bh[iw]) + abs(target)
+                w_D[iw] = 1.0
+                w_D_m[iw] = 1.0
+                w_C.append(np.zeros((n_w, nb)))
+                w_C_m.append(np.zeros((n_w, nb)))
+            else:
+                sgn = -1.0 if w.kind == 0 else 1.0
+                q = qs[ph]
+                w_res[iw] = sgn * q.v.sum() - target
+                w_res_m[iw] = q.m.sum() + abs(target)
+                w_D[iw] = sgn * q.g[:, L].sum()
+                w_D_m[iw] = q.gm[:, L].sum()
+                c_blk = np.zeros((n_w, nb))
+                c_blk[:, :nv] = sgn * q.g[:, :nv]
+                c_mag = np.zeros((n_w, nb))
+                c_mag[:, :nv] = q.gm[:, :nv]
+                w_C.append(c_blk)
+                w_C_m.append(c_mag)
 
     out = {
         "R": R, "R_mag": Rm, "row_ptr": row_ptr, "col_idx": col_idx,
@@ -276,6 +332,10 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None)
         "face_flux": face_flux, "face_flux_mag": face_flux_mag,
         "face_dphi": face_dphi,
     }
+    if unknown_bhp:
+        cat = lambda parts: np.concatenate(parts) if parts else np.zeros((0, nb))
+        out.update(well_res=w_res, well_res_mag=w_res_m, well_D=w_D, well_D_mag=w_D_m,
+                   well_B=cat(w_B), well_B_mag=cat(w_B_m), well_C=cat(w_C), well_C_mag=cat(w_C_m))
     if gw is not None:
         out["g_unew"] = gw[:, :nv].T.copy()
         out["g_uold"] = gw[:, nv:2 * nv].T.copy()

@@ -36,7 +36,7 @@ MUTATIONS = [
      'gamma = (Pi["rho_" + a] + Pi["rho_" + a]) * (0.5 * GRAV)'),              # wrong index
     ("linearize.py", "half_j = (0.5 * h) / kj", "half_j = (0.5 * h) * kj"),    # harmonic mean
     ("linearize.py", "(mn[e] - mo[e]) * (vol / RB_FT3) / dt", "(mn[e] - mo[e]) * (vol / RB_FT3) * dt"),
-    ("linearize.py", '(w.p_bh - P["p_o"])', '(P["p_o"] - w.p_bh)'),            # producer sign
+    ("linearize.py", '(pw - P["p_o"])', '(P["p_o"] - pw)'),                    # producer sign
     ("linearize.py", 'np.add.at(R[:, e], rows, sign * q.v)', 'np.add.at(R[:, e], rows, q.v)'),
     ("blackoil.py", "- (kr_w + kr_g))", ")"),                                   # Stone II term
     ("blackoil.py", 'out["p_w"] = p - pc_ow', 'out["p_w"] = p + pc_ow'),        # Pc sign
