@@ -273,8 +273,8 @@ ocp_status ocp_bicgstab(ocp_grid* grid, const double* bsr_val, const double* b, 
  * S_g falls below zero becomes undersaturated with X = R_s,sat(p); an
  * undersaturated cell whose R_s exceeds R_s,sat(p) becomes saturated with
  * S_g = 0.  Writes the largest |du| applied per variable to du_max (device,
- * nb + 1 doubles: p, S_w, S_g, R_s) and the number of switched cells to
- * *nswitch (device int). */
+ * nb + 1 doubles: p, S_w, then S_g and R_s with three phases; the third is
+ * zero with two) and the number of switched cells to *nswitch (device int). */
 ocp_status ocp_newton_update(ocp_grid* grid, double* u, int8_t* flag, const double* du, double scale,
                              double ds_max, double* du_max, int* nswitch, void* cuda_stream);
 
@@ -287,6 +287,72 @@ ocp_status ocp_well_rates_vjp(ocp_grid* grid, const double* u, const int8_t* fla
 /* Recomputes the transmissibilities, their ln k weights and the well indices
  * from a new permeability field lnk[N] (device), as ocp_grid_create did. */
 ocp_status ocp_grid_update_perm(ocp_grid* grid, const double* lnk, void* cuda_stream);
+
+/* ---------------------------------------------------------------- wells as unknowns
+ * The global Jacobian of Sec. 3.4.1 has rows and columns for the wells: each
+ * well's bottom-hole pressure p_bh is an unknown with one equation, set by the
+ * well's control (AllWells monitors the well pressure, Sec. 3.2.4).  A control
+ * is a device array of nwell ocp_well_ctrl:
+ *   mode 0: pressure control, R_w = p_bh - target (psi);
+ *   mode 1: surface-rate control of component `phase` (0 water, 1 oil,
+ *           nb-1 gas incl. dissolved gas), R_w = s sum_perf q_phase - target
+ *           with s = -1 for producers (production positive), +1 for injectors;
+ *   limit:  the pressure a rate-controlled producer may not fall below, or an
+ *           injector may not rise above (ocp_well_update).
+ * Perforation-indexed arrays follow the wells in order and each well's
+ * perforations in the order of ocp_well.cells (nperf = sum of nperf). */
+typedef struct {
+  int32_t mode;
+  int32_t phase;
+  double target;
+  double limit;
+} ocp_well_ctrl;
+
+/* ocp_linearize with the perforation sources evaluated at p_bh[nwell]
+ * (device) instead of each well's fixed ocp_well.p_bh, plus the well rows and
+ * columns: well_res[nwell] = R_w, well_b[nperf*nb] = dR_cell/dp_bh (row e of
+ * the perforated cell), well_c[nperf*nb] = dR_w/du_cell (variable v of the
+ * perforated cell; zero under pressure control) and well_d[nwell] =
+ * dR_w/dp_bh (1 under pressure control).  All device, caller-owned.  A
+ * control with a mode other than 0 and 1, a phase outside [0, nb), or rate
+ * control of a well without perforations sets the sticky status
+ * OCP_ERR_INVALID_ARG and is treated as pressure control. */
+ocp_status ocp_linearize_wells(ocp_grid* grid, const double* u_new, const int8_t* flag_new,
+                               const double* u_old, const int8_t* flag_old, double dt, const double* p_bh,
+                               const ocp_well_ctrl* ctrl, double* residual, double* bsr_val, double* face_flux,
+                               double* well_res, double* well_b, double* well_c, double* well_d,
+                               void* cuda_stream);
+
+/* Solves the system with well unknowns, [A B; C D][x; x_w] = [b; b_w]
+ * (transposed: [A^T C^T; B^T D]), by eliminating the well unknowns: BiCGSTAB
+ * as in ocp_bicgstab on the Schur complement A - B D^-1 C, applied next to
+ * the block-CSR product (its block-Jacobi blocks include the perforated
+ * cells' rank-one terms), with b - B D^-1 b_w, then x_w = D^-1 (b_w - C x).
+ * B, C, D as written by ocp_linearize_wells; b, x [nb*N] block-interleaved,
+ * b_w, x_w [nwell]; x holds the initial guess.  work: ocp_solver_work_doubles().
+ * Every D entry must be nonzero (a rate-controlled well needs an open
+ * perforation).  Errors as ocp_bicgstab; x_w is written in every case. */
+ocp_status ocp_bicgstab_wells(ocp_grid* grid, const double* bsr_val, const double* well_b,
+                              const double* well_c, const double* well_d, const double* b, const double* b_w,
+                              double* x, double* x_w, double rtol, int maxit, int transpose, double* work,
+                              int* iters, double* relres, void* cuda_stream);
+
+/* p_bh += scale * dp (device, nwell), then the pressure monitoring: a
+ * rate-controlled producer whose p_bh fell below its limit, or injector whose
+ * p_bh rose above it, changes to pressure control (ctrl is updated in place:
+ * mode 0, target = limit) with p_bh = limit.  Writes max |scale dp| to
+ * *dp_max and the number of switched wells to *nswitch (both device). */
+ocp_status ocp_well_update(ocp_grid* grid, double* p_bh, const double* dp, double scale, ocp_well_ctrl* ctrl,
+                           double* dp_max, int* nswitch, void* cuda_stream);
+
+/* Convergence measures of a linearisation (Sec. 3.2.5, step 4): norms[e] =
+ * max over cells of |R[c*nb+e]| / (phi_c V_c / dt), V in reservoir barrels,
+ * for e < nb; norms[3] = max over wells of |R_w| / max(|target|, 1) for
+ * rate control and |R_w| for pressure control (0 without wells).  norms is a
+ * device array of 4 doubles; maxima of non-negative values are exact and
+ * independent of the order of evaluation. */
+ocp_status ocp_residual_norms(ocp_grid* grid, const double* residual, double dt, const double* well_res,
+                              const ocp_well_ctrl* ctrl, double* norms, void* cuda_stream);
 
 /* ---------------------------------------------------------------- adaptive coupling
  * The adaptively coupled domain decomposition of Sec. 4 decides at the start

@@ -377,6 +377,7 @@ ocp_status ocp_get_status(ocp_grid* g, void* stream) {
   if (h & ocp::kStatNonFinite) return fail(OCP_ERR_NONFINITE, "a kernel met a non-finite value");
   if (h & ocp::kStatBadFlag) return fail(OCP_ERR_INVALID_ARG, "a phase-state flag was neither 0 nor 1");
   if (h & ocp::kStatTimeout) return fail(OCP_ERR_TIMEOUT, "a bounded device wait expired");
+  if (h & ocp::kStatBadControl) return fail(OCP_ERR_INVALID_ARG, "a well control was invalid");
   return OCP_OK;
 }
 

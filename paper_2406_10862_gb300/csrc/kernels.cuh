@@ -7,7 +7,7 @@ namespace ocp {
 int64_t linearize_scratch_doubles(int64_t N);
 cudaError_t launch_linearize(const ocp_grid* g, const double* u_new, const int8_t* f_new,
                              const double* u_old, const int8_t* f_old, double dt, double* res,
-                             double* val, double* face_flux, cudaStream_t s);
+                             double* val, double* face_flux, cudaStream_t s, const double* p_bh = nullptr);
 // The same launches with the per-cell scratch given explicitly (used by the
 // entry point that must not allocate).
 cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const double* u_new,
@@ -16,6 +16,25 @@ cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const d
 ocp_status report(ocp_status st, const char* fmt, ...);
 cudaError_t launch_perf_wi(ocp_grid* g, const double* lnk, cudaStream_t s);
 int64_t solver_work_doubles(const ocp_grid* g);
+
+// Well terms of a Jacobian with bottom-hole-pressure unknowns, oriented for
+// the system being solved: bs couples the wells into the cell rows, cs the
+// cells into the well rows (nb values per perforation each), d the well
+// diagonal (one per well).
+struct WellSchur {
+  const double* bs;
+  const double* cs;
+  const double* d;
+};
+// mode 0: out += alpha bs (d^-1 (cs . in)); 1: out += alpha bs (d^-1 bw);
+// 2: xw = d^-1 (bw - cs . in)
+cudaError_t launch_well_schur(const ocp_grid* g, const WellSchur& ws, int mode, double alpha, const double* in,
+                              double* out, const double* bw, double* xw, cudaStream_t s);
+// Left block-Jacobi BiCGSTAB on A (ws == nullptr) or on the Schur complement
+// A - bs d^-1 cs of the well unknowns.
+ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, const double* b, double* x,
+                        double rtol, int maxit, int transpose, double* work, int* iters, double* relres,
+                        cudaStream_t s);
 cudaError_t launch_tiles(int nb, const TileList* lists, const ModelArgs& single, const LaunchCfg& cfg,
                          int sms, cudaStream_t s);
 ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,

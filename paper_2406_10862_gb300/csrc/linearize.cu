@@ -93,7 +93,9 @@ __device__ __forceinline__ void cell_body(const ModelArgs& M, const Table& T, lo
   }
   if (ip >= 0) {
     double src[3], ds[3][3];
-    well_source<NB>(M.perf[ip], q, a, src, ds);
+    Perf w = M.perf[ip];
+    if (M.p_bh) w.p_bh = M.p_bh[w.well];
+    well_source<NB>(w, q, a, src, ds);
     for (int e = 0; e < NB; ++e) {
       r[e] -= src[e];
       for (int v = 0; v < NB; ++v) dg[e][v] -= ds[e][v];
@@ -331,6 +333,7 @@ ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, co
   M.val = val;
   M.face_flux = face_flux;
   M.scale = g->prm.vol_rb / dt;
+  M.p_bh = nullptr;
   return M;
 }
 
@@ -338,8 +341,9 @@ namespace {
 
 cudaError_t launch_single(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
                           const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
-                          double* face_flux, cudaStream_t s) {
-  const ModelArgs M = model_args(g, scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux);
+                          double* face_flux, cudaStream_t s, const double* p_bh = nullptr) {
+  ModelArgs M = model_args(g, scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux);
+  M.p_bh = p_bh;
   TileList lists[2];
   lists[0].models = nullptr;
   lists[0].tiles = nullptr;
@@ -356,8 +360,8 @@ int64_t linearize_scratch_doubles(int64_t N) { return (int64_t)100 * N; }
 
 cudaError_t launch_linearize(const ocp_grid* g, const double* u_new, const int8_t* f_new,
                              const double* u_old, const int8_t* f_old, double dt, double* res,
-                             double* val, double* face_flux, cudaStream_t s) {
-  return launch_single(g, g->d_scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s);
+                             double* val, double* face_flux, cudaStream_t s, const double* p_bh) {
+  return launch_single(g, g->d_scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s, p_bh);
 }
 
 cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const double* u_new,

@@ -98,9 +98,13 @@ __global__ void upd_xr(long long n, double* __restrict__ x, const double* __rest
 }
 
 // Inverse of every diagonal block (of its transpose when TRANS).
+// With well terms, a perforated cell's block is that of the Schur complement,
+// A_cc - bs_c cs_c^T / d_w.
 template <int NB>
 __global__ void block_jacobi_kernel(Params P, const int32_t* __restrict__ row_ptr, const double* __restrict__ val,
-                                    double* __restrict__ dinv, int trans, int* status) {
+                                    double* __restrict__ dinv, int trans, int* status,
+                                    const int32_t* __restrict__ perf_of_cell, const Perf* __restrict__ perf,
+                                    WellSchur ws) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= P.N) return;
   int i, j, k;
@@ -110,6 +114,14 @@ __global__ void block_jacobi_kernel(Params P, const int32_t* __restrict__ row_pt
   double a[NB][NB], inv[NB][NB];
   for (int e = 0; e < NB; ++e)
     for (int v = 0; v < NB; ++v) a[e][v] = trans ? D[v * NB + e] : D[e * NB + v];
+  if (ws.d) {
+    const int ip = perf_of_cell[c];
+    if (ip >= 0) {
+      const double id = 1.0 / ws.d[perf[ip].well];
+      for (int e = 0; e < NB; ++e)
+        for (int v = 0; v < NB; ++v) a[e][v] = fma(-ws.bs[ip * NB + e] * id, ws.cs[ip * NB + v], a[e][v]);
+    }
+  }
   double det;
   if (NB == 3) {
     const double c00 = a[1][1] * a[2][2] - a[1][2] * a[2][1];
@@ -249,7 +261,106 @@ cudaError_t launch_perf_wi(ocp_grid* g, const double* lnk, cudaStream_t s) {
 
 int64_t solver_work_doubles(const ocp_grid* g) {
   const int64_t n = (int64_t)g->prm.nb * g->prm.N;
-  return 8 * n + (int64_t)g->prm.nb * g->prm.nb * g->prm.N + kRedBlocks + S_COUNT + 8;
+  // r, r0, p, v, s, t, y, z; block inverses; partial sums; scalars; and the
+  // reduced right-hand side of the well elimination
+  return 9 * n + (int64_t)g->prm.nb * g->prm.nb * g->prm.N + kRedBlocks + S_COUNT + 8;
+}
+
+ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, const double* b, double* x,
+                        double rtol, int maxit, int transpose, double* work, int* iters, double* relres,
+                        cudaStream_t s) {
+  if (!(rtol > 0.0) || maxit < 1) return report(OCP_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 1");
+  const int nb = g->prm.nb;
+  const long long N = g->prm.N, n = nb * N;
+  double* r = work;
+  double* r0 = r + n;
+  double* p = r0 + n;
+  double* v = p + n;
+  double* sv = v + n;
+  double* t = sv + n;
+  double* y = t + n;
+  double* z = y + n;
+  double* dinv = z + n;
+  double* part = dinv + (long long)nb * nb * N;
+  double* sc = part + kRedBlocks;
+  const unsigned bn = nblk(n), bc = nblk(N);
+  auto dot = [&](const double* a, const double* c, int slot) {
+    dot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, a, c, part);
+    dot_final<<<1, kRedThreads, 0, s>>>(part, sc + slot);
+  };
+  auto apply = [&](const double* in, double* out) {
+    if (nb == 3) bj_apply_kernel<3><<<bc, 256, 0, s>>>(N, dinv, in, out);
+    else bj_apply_kernel<2><<<bc, 256, 0, s>>>(N, dinv, in, out);
+  };
+  cudaError_t e = cudaSuccess;
+  const WellSchur wsv = ws ? *ws : WellSchur{nullptr, nullptr, nullptr};
+  if (nb == 3)
+    block_jacobi_kernel<3><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status,
+                                              g->d_perf_of_cell, g->d_perf, wsv);
+  else
+    block_jacobi_kernel<2><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status,
+                                              g->d_perf_of_cell, g->d_perf, wsv);
+  // the operator: A, or A - bs d^-1 cs with well terms
+  auto op = [&](const double* in, double* out) {
+    cudaError_t err = launch_spmv(g, val, 1.0, in, 0.0, out, transpose, s);
+    if (err == cudaSuccess && ws) err = launch_well_schur(g, *ws, 0, -1.0, in, out, nullptr, nullptr, s);
+    return err;
+  };
+  // Left block-Jacobi preconditioning: BiCGSTAB on D^-1 A x = D^-1 b, so the
+  // residual that is tested is scaled cell by cell into the units of the
+  // unknowns (psi, saturation, scf/stb) and no equation dominates its norm.
+  // y = D^-1 b and r = D^-1 (b - A x)
+  apply(b, y);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = launch_spmv(g, val, -1.0, x, 1.0, t, transpose, s);
+  if (e == cudaSuccess && ws) e = launch_well_schur(g, *ws, 0, 1.0, x, t, nullptr, nullptr, s);
+  apply(t, r);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r0, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * n, s);
+  scal_init<<<1, 1, 0, s>>>(sc);
+  dot(y, y, S_BB);
+  dot(r, r, S_RR);
+  double h[S_COUNT];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab: %s", cudaGetErrorString(e));
+  const double bnorm = std::sqrt(h[S_BB]);
+  double res = std::sqrt(h[S_RR]);
+  int it = 0;
+  const double target = rtol * (bnorm > 0.0 ? bnorm : 1.0);
+  while (res > target && it < maxit) {
+    ++it;
+    dot(r0, r, S_RHO);
+    scal_beta<<<1, 1, 0, s>>>(sc);
+    upd_p<<<bn, 256, 0, s>>>(n, r, p, v, sc);
+    // v = D^-1 A p
+    e = op(p, z);
+    apply(z, v);
+    dot(r0, v, S_R0V);
+    scal_alpha<<<1, 1, 0, s>>>(sc);
+    upd_s<<<bn, 256, 0, s>>>(n, r, v, sv, sc);
+    // t = D^-1 A s
+    if (e == cudaSuccess) e = op(sv, z);
+    apply(z, t);
+    dot(t, sv, S_TS);
+    dot(t, t, S_TT);
+    scal_omega<<<1, 1, 0, s>>>(sc);
+    // x += alpha p + omega s;  r = s - omega t
+    upd_xr<<<bn, 256, 0, s>>>(n, x, p, sv, r, sv, t, sc);
+    dot(r, r, S_RR);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab: %s", cudaGetErrorString(e));
+    res = std::sqrt(h[S_RR]);
+    if (h[S_FLAG] != 0.0 || !std::isfinite(res)) break;
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = bnorm > 0.0 ? res / bnorm : res;
+  if (!std::isfinite(res)) return report(OCP_ERR_NONFINITE, "ocp_bicgstab: non-finite residual");
+  if (res > target) return report(OCP_ERR_TIMEOUT, "ocp_bicgstab: no convergence in %d iterations (relres %.3e)",
+                                  it, bnorm > 0.0 ? res / bnorm : res);
+  return OCP_OK;
 }
 
 }  // namespace ocp
@@ -279,90 +390,10 @@ ocp_status ocp_bicgstab(ocp_grid* g, const double* val, const double* b, double*
                         int transpose, double* work, int* iters, double* relres, void* stream) {
   using namespace ocp;
   if (!g || !val || !b || !x || !work) return report(OCP_ERR_INVALID_ARG, "grid, val, b, x and work are required");
-  if (!(rtol > 0.0) || maxit < 1) return report(OCP_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 1");
   if (b == x) return report(OCP_ERR_INVALID_ARG, "b and x must not overlap");
   Guard guard(g->device);
   if (guard.err != cudaSuccess) return report(OCP_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(guard.err));
-  cudaStream_t s = (cudaStream_t)stream;
-  const int nb = g->prm.nb;
-  const long long N = g->prm.N, n = nb * N;
-  double* r = work;
-  double* r0 = r + n;
-  double* p = r0 + n;
-  double* v = p + n;
-  double* sv = v + n;
-  double* t = sv + n;
-  double* y = t + n;
-  double* z = y + n;
-  double* dinv = z + n;
-  double* part = dinv + (long long)nb * nb * N;
-  double* sc = part + kRedBlocks;
-  const unsigned bn = nblk(n), bc = nblk(N);
-  auto dot = [&](const double* a, const double* c, int slot) {
-    dot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, a, c, part);
-    dot_final<<<1, kRedThreads, 0, s>>>(part, sc + slot);
-  };
-  auto apply = [&](const double* in, double* out) {
-    if (nb == 3) bj_apply_kernel<3><<<bc, 256, 0, s>>>(N, dinv, in, out);
-    else bj_apply_kernel<2><<<bc, 256, 0, s>>>(N, dinv, in, out);
-  };
-  cudaError_t e = cudaSuccess;
-  if (nb == 3) block_jacobi_kernel<3><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status);
-  else block_jacobi_kernel<2><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status);
-  // Left block-Jacobi preconditioning: BiCGSTAB on D^-1 A x = D^-1 b, so the
-  // residual that is tested is scaled cell by cell into the units of the
-  // unknowns (psi, saturation, scf/stb) and no equation dominates its norm.
-  // y = D^-1 b and r = D^-1 (b - A x)
-  apply(b, y);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(t, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = launch_spmv(g, val, -1.0, x, 1.0, t, transpose, s);
-  apply(t, r);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(r0, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, sizeof(double) * n, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * n, s);
-  scal_init<<<1, 1, 0, s>>>(sc);
-  dot(y, y, S_BB);
-  dot(r, r, S_RR);
-  double h[S_COUNT];
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab: %s", cudaGetErrorString(e));
-  const double bnorm = std::sqrt(h[S_BB]);
-  double res = std::sqrt(h[S_RR]);
-  int it = 0;
-  const double target = rtol * (bnorm > 0.0 ? bnorm : 1.0);
-  while (res > target && it < maxit) {
-    ++it;
-    dot(r0, r, S_RHO);
-    scal_beta<<<1, 1, 0, s>>>(sc);
-    upd_p<<<bn, 256, 0, s>>>(n, r, p, v, sc);
-    // v = D^-1 A p
-    e = launch_spmv(g, val, 1.0, p, 0.0, z, transpose, s);
-    apply(z, v);
-    dot(r0, v, S_R0V);
-    scal_alpha<<<1, 1, 0, s>>>(sc);
-    upd_s<<<bn, 256, 0, s>>>(n, r, v, sv, sc);
-    // t = D^-1 A s
-    if (e == cudaSuccess) e = launch_spmv(g, val, 1.0, sv, 0.0, z, transpose, s);
-    apply(z, t);
-    dot(t, sv, S_TS);
-    dot(t, t, S_TT);
-    scal_omega<<<1, 1, 0, s>>>(sc);
-    // x += alpha p + omega s;  r = s - omega t
-    upd_xr<<<bn, 256, 0, s>>>(n, x, p, sv, r, sv, t, sc);
-    dot(r, r, S_RR);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab: %s", cudaGetErrorString(e));
-    res = std::sqrt(h[S_RR]);
-    if (h[S_FLAG] != 0.0 || !std::isfinite(res)) break;
-  }
-  if (iters) *iters = it;
-  if (relres) *relres = bnorm > 0.0 ? res / bnorm : res;
-  if (!std::isfinite(res)) return report(OCP_ERR_NONFINITE, "ocp_bicgstab: non-finite residual");
-  if (res > target) return report(OCP_ERR_TIMEOUT, "ocp_bicgstab: no convergence in %d iterations (relres %.3e)",
-                                  it, bnorm > 0.0 ? res / bnorm : res);
-  return OCP_OK;
+  return bicgstab_run(g, val, nullptr, b, x, rtol, maxit, transpose, work, iters, relres, (cudaStream_t)stream);
 }
 
 ocp_status ocp_newton_update(ocp_grid* g, double* u, int8_t* flag, const double* du, double scale,

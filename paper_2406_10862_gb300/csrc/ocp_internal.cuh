@@ -23,7 +23,7 @@ constexpr double kDarcy = 0.001127;    // rb cP / (day psi mD ft)
 constexpr double kGrav = 1.0 / 144.0;  // psi per (lb/ft^3 ft)
 
 // Sticky device status bits (ocp_get_status maps them to ocp_status).
-enum : int { kStatNonFinite = 1, kStatBadFlag = 2, kStatTimeout = 4 };
+enum : int { kStatNonFinite = 1, kStatBadFlag = 2, kStatTimeout = 4, kStatBadControl = 8 };
 
 // Preprocessed PVT table: knots and, per linear piece k, value and slope of
 // b_o = 1/B_o, 1/mu_o, b_g = 1/B_g, 1/mu_g and R_s versus p, plus the inverse
@@ -129,6 +129,7 @@ struct ModelArgs {
   double* val;
   double* face_flux;
   double scale;              // bulk volume in rb / dt
+  const double* p_bh;        // per-well bottom-hole pressures, or null for each perforation's own
 };
 
 // Tiles of `TPB` consecutive cells: with models == nullptr the single model

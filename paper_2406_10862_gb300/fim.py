@@ -3,7 +3,11 @@
 The FIM nonlinear iteration of Sec. 3.2.5 -- linearise (``ocp_linearize``),
 solve (``ocp_bicgstab``), update with chop and phase switch
 (``ocp_newton_update``), test convergence -- repeated over time steps, and the
-reverse pass of a loss on the well rates.  The gradient with respect to the
+reverse pass of a loss on the well rates.  ``Stepper.step_wells`` runs the
+same iteration with the wells' bottom-hole pressures as unknowns under
+pressure or rate control (``ocp_linearize_wells``, ``ocp_bicgstab_wells``,
+``ocp_well_update``) and a residual-norm convergence test
+(``ocp_residual_norms``).  The gradient with respect to the
 log-permeability field is
 
     dL/d ln k = sum_n [ dl_n/d ln k - lambda_n^T dR_n/d ln k ],
@@ -41,6 +45,8 @@ class NewtonOptions:
     tol_s: float = 1e-10         # saturation
     max_newton: int = 30
     ds_max: float = 0.2
+    tol_cnv: float = 1e-9        # scaled residual, per pore volume (with well unknowns)
+    tol_well: float = 1e-9       # well residual, relative to the rate target (psi under pressure control)
 
 
 class Stepper:
@@ -73,11 +79,52 @@ class Stepper:
             d = self.dmax.cpu().tolist()
             nsw = int(self.nsw.item())
             self.newton_iters += 1
-            if nsw == 0 and d[0] < o.tol_p and d[1] < o.tol_s and d[2] < o.tol_s and d[3] < o.tol_p:
+            # du_max holds nb + 1 maxima: p, S_w, then S_g and R_s with three phases
+            small = d[0] < o.tol_p and d[1] < o.tol_s and (g.nb == 2 or (d[2] < o.tol_s and d[3] < o.tol_p))
+            if nsw == 0 and small:
                 st = g.status()
                 if st != 0:
                     raise NewtonFailure("device status %d" % st)
                 return u, f
+        raise NewtonFailure("Newton did not converge in %d iterations" % o.max_newton)
+
+    def step_wells(self, u_old, f_old, dt, p_bh, ctrl):
+        """One step with the bottom-hole pressures as unknowns (``ctrl`` is a
+        device ocp_well_ctrl array, see ``ocp.well_controls``; a well that
+        reaches its pressure limit is switched to pressure control in it).
+        Converged when the scaled residuals (``ocp_residual_norms``) are below
+        tol_cnv / tol_well at an iterate whose update switched nothing.
+        Returns (u, flag, p_bh, linearisations)."""
+        g, o = self.g, self.o
+        nb, nw = g.nb, g.nwell
+        u, f, p = u_old.clone(), f_old.clone(), p_bh.clone()
+        if not hasattr(self, "_wb"):
+            self._wb = {"residual": self.r, "bsr_val": self.val, "well_res": g.empty(max(nw, 1)),
+                        "well_b": g.empty(max(g.nperf, 1) * nb), "well_c": g.empty(max(g.nperf, 1) * nb),
+                        "well_d": g.empty(max(nw, 1))}
+            self._dp = g.empty(max(nw, 1))
+            self._norms = g.empty(4)
+            self._dpmax = g.empty(1)
+            self._nsw_w = torch.zeros(1, dtype=torch.int32, device=g.device)
+        wb = self._wb
+        nsw = 1
+        for it in range(1, o.max_newton + 1):
+            g.linearize_wells(u, f, u_old, f_old, dt, p, ctrl, out=wb)
+            nrm = g.residual_norms(wb["residual"], dt, wb["well_res"], ctrl, self._norms).cpu().tolist()
+            if nsw == 0 and max(nrm[:nb]) < o.tol_cnv and nrm[3] < o.tol_well:
+                st = g.status()
+                if st != 0:
+                    raise NewtonFailure("device status %d" % st)
+                return u, f, p, it
+            self.du.zero_()
+            self._dp.zero_()
+            _, li, _ = g.bicgstab_wells(wb["bsr_val"], wb["well_b"], wb["well_c"], wb["well_d"], wb["residual"],
+                                        wb["well_res"], self.du, self._dp, o.rtol, o.maxit, work=self.work)
+            self.linear_iters += li
+            g.newton_update(u, f, self.du, -1.0, o.ds_max, self.dmax, self.nsw)
+            g.well_update(p, self._dp, -1.0, ctrl, self._dpmax, self._nsw_w)
+            self.newton_iters += 1
+            nsw = int(self.nsw.item()) + int(self._nsw_w.item())
         raise NewtonFailure("Newton did not converge in %d iterations" % o.max_newton)
 
     def linearize_at(self, u, f, u_old, f_old, dt):

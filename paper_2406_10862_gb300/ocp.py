@@ -30,7 +30,27 @@ EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_patt
            "ocp_batch_set_io", "ocp_batch_linearize", "ocp_batch_graph_launch", "ocp_batch_tune",
            "ocp_batch_set_shape", "ocp_batch_get_shape", "ocp_batch_get_status", "ocp_grid_set_shape",
            "ocp_solver_work_doubles", "ocp_bicgstab", "ocp_newton_update", "ocp_well_rates_vjp",
-           "ocp_grid_update_perm", "ocp_coupling_work_ints", "ocp_coupling_components", "ocp_bsr_spmv", "ocp_adjoint_vjp", "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
+           "ocp_grid_update_perm", "ocp_coupling_work_ints", "ocp_coupling_components", "ocp_linearize_wells",
+           "ocp_bicgstab_wells", "ocp_well_update", "ocp_residual_norms", "ocp_bsr_spmv", "ocp_adjoint_vjp",
+           "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
+
+# ocp_well_ctrl: int32 mode, int32 phase, double target, double limit (24 bytes)
+CTRL_DTYPE = np.dtype([("mode", "<i4"), ("phase", "<i4"), ("target", "<f8"), ("limit", "<f8")])
+
+
+def well_controls(controls, limits, device):
+    """Device array of ocp_well_ctrl from (mode, phase, target) tuples and limits."""
+    a = np.zeros(len(controls), dtype=CTRL_DTYPE)
+    for i, ((mode, phase, target), lim) in enumerate(zip(controls, limits)):
+        a[i] = (int(mode), int(phase), float(target), float(lim))
+    raw = np.frombuffer(a.tobytes(), dtype=np.uint8) if len(a) else np.zeros(0, dtype=np.uint8)
+    return torch.as_tensor(raw.copy(), device=device)
+
+
+def read_controls(ctrl):
+    """(mode, phase, target, limit) tuples of a device ocp_well_ctrl array."""
+    a = np.frombuffer(ctrl.cpu().numpy().tobytes(), dtype=CTRL_DTYPE)
+    return [(int(r["mode"]), int(r["phase"]), float(r["target"]), float(r["limit"])) for r in a]
 
 
 class OcpError(RuntimeError):
@@ -118,6 +138,12 @@ def load(build_if_missing: bool = False):
                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp]
     lib.ocp_newton_update.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
     lib.ocp_well_rates_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.ocp_linearize_wells.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.ocp_bicgstab_wells.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_double), vp]
+    lib.ocp_well_update.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp, vp]
+    lib.ocp_residual_norms.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp, vp]
     lib.ocp_grid_update_perm.argtypes = [vp, vp, vp]
     lib.ocp_coupling_work_ints.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.ocp_coupling_work_ints.restype = ctypes.c_int64
@@ -207,6 +233,7 @@ class Grid:
         _check(lib.ocp_grid_info(h, ctypes.byref(n), ctypes.byref(nb), ctypes.byref(nnzb)))
         self.N, self.nb, self.nnzb = n.value, nb.value, nnzb.value
         self.nwell = len(desc.wells)
+        self.nperf = int(sum(len(w.cells) for w in desc.wells))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -343,6 +370,62 @@ class Grid:
     def update_perm(self, lnk, stream=None):
         self._t(lnk, self.N, torch.float64, "lnk")
         _check(load().ocp_grid_update_perm(self._h, _ptr(lnk), _stream(self.device, stream)))
+
+    # ------------------------------------------------------------ wells as unknowns
+    def linearize_wells(self, u_new, flag_new, u_old, flag_old, dt, p_bh, ctrl, out=None, want_face_flux=False,
+                        stream=None):
+        """``ocp_linearize_wells``.  Returns a dict with residual, bsr_val,
+        face_flux (or None), well_res, well_b, well_c, well_d."""
+        N, nb, nw, npf = self.N, self.nb, self.nwell, self.nperf
+        self._t(u_new, nb * N, torch.float64, "u_new")
+        self._t(u_old, nb * N, torch.float64, "u_old")
+        if nb == 3 or flag_new is not None:
+            self._t(flag_new, N, torch.int8, "flag_new")
+            self._t(flag_old, N, torch.int8, "flag_old")
+        self._t(p_bh, nw, torch.float64, "p_bh")
+        self._t(ctrl, 24 * nw, torch.uint8, "ctrl")
+        o = dict(out or {})
+        sizes = {"residual": nb * N, "bsr_val": self.nnzb * nb * nb, "well_res": max(nw, 1),
+                 "well_b": max(npf, 1) * nb, "well_c": max(npf, 1) * nb, "well_d": max(nw, 1)}
+        for k, n in sizes.items():
+            if k not in o:
+                o[k] = self.empty(n)
+            self._t(o[k], n, torch.float64, k)
+        if want_face_flux and o.get("face_flux") is None:
+            o["face_flux"] = self.empty(3 * nb * N)
+        ff = o.get("face_flux")
+        self._t(ff, 3 * nb * N, torch.float64, "face_flux", allow_none=True)
+        _check(load().ocp_linearize_wells(self._h, _ptr(u_new), _ptr(flag_new), _ptr(u_old), _ptr(flag_old),
+                                          float(dt), _ptr(p_bh), _ptr(ctrl), _ptr(o["residual"]),
+                                          _ptr(o["bsr_val"]), _ptr(ff), _ptr(o["well_res"]), _ptr(o["well_b"]),
+                                          _ptr(o["well_c"]), _ptr(o["well_d"]), _stream(self.device, stream)))
+        o["face_flux"] = ff
+        return o
+
+    def bicgstab_wells(self, bsr_val, well_b, well_c, well_d, b, b_w, x, x_w, rtol, maxit, transpose=False,
+                       work=None, stream=None, check=True):
+        """Solve [A B; C D][x; x_w] = [b; b_w] (transposed with ``transpose``)
+        through the Schur complement of the well unknowns; x is the initial
+        guess.  Returns (status, iterations, relative residual)."""
+        work = work if work is not None else self.solver_work()
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        st = load().ocp_bicgstab_wells(self._h, _ptr(bsr_val), _ptr(well_b), _ptr(well_c), _ptr(well_d), _ptr(b),
+                                       _ptr(b_w), _ptr(x), _ptr(x_w), float(rtol), int(maxit),
+                                       int(bool(transpose)), _ptr(work), ctypes.byref(it), ctypes.byref(rr),
+                                       _stream(self.device, stream))
+        if check:
+            _check(st)
+        return st, it.value, rr.value
+
+    def well_update(self, p_bh, dp, scale, ctrl, dp_max, nswitch, stream=None):
+        _check(load().ocp_well_update(self._h, _ptr(p_bh), _ptr(dp), float(scale), _ptr(ctrl), _ptr(dp_max),
+                                      _ptr(nswitch), _stream(self.device, stream)))
+
+    def residual_norms(self, residual, dt, well_res, ctrl, norms=None, stream=None):
+        norms = norms if norms is not None else self.empty(4)
+        _check(load().ocp_residual_norms(self._h, _ptr(residual), float(dt), _ptr(well_res), _ptr(ctrl),
+                                         _ptr(norms), _stream(self.device, stream)))
+        return norms
 
     def coupling_components(self, u_new, flag_new, u_old, flag_old, threshold, px, py, pz, labels=None,
                             work=None, stream=None):
