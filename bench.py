@@ -374,6 +374,7 @@ def run_gpu(args, rank, world, local_rank):
             line["small_case"] = run_small_case(dev, local_rank)
             line["oil_water"] = run_oil_water(dev, local_rank)
             line["adjoint"] = run_adjoint(dev, local_rank)
+            line["wells"] = run_wells(dev, local_rank)
             line["coupling"] = run_coupling(dev, local_rank, with_oracle=(world == 1 and not args.no_cpu_baseline))
         if world == 1 and not args.no_cpu_baseline:
             t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s)
@@ -539,6 +540,72 @@ def run_oil_water(dev, local_rank, steps=10):
             "spmv_gflops": 2.0 * 4 * nnzb / (statistics.mean(spm) * 1e-3) / 1e9, "device_status": st}
 
 
+def run_wells(dev, local_rank, reps=20):
+    """One backward-Euler step of the 200 000-cell box with every well on
+    surface-rate control (producers: half their oil rate at 3500 psi, limit
+    1000 psi; injector: half its gas rate at 5500 psi, limit 8000 psi), the
+    bottom-hole pressures as unknowns: Newton iterations of
+    ocp_linearize_wells + ocp_residual_norms + ocp_bicgstab_wells +
+    updates.  Also the linearisation with well rows against the plain one."""
+    import numpy as np
+    import torch
+
+    from paper_2406_10862_gb300 import fim, ocp, workloads as W
+
+    g, s = W.layered_box()
+    grid = ocp.Grid(g, local_rank)
+    nb, nw = grid.nb, grid.nwell
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    un, fn = T(s.u_old.ravel()), T(s.flag_old)
+    q = grid.well_rates(un, fn).view(nw, nb).cpu().numpy()
+    ctrl, lim, p0 = [], [], []
+    for iw, w in enumerate(g.wells):
+        if w.kind == 0:
+            ctrl.append((1, 1, 0.5 * -q[iw, 1]))
+            lim.append(1000.0)
+        else:
+            ctrl.append((1, nb - 1, 0.5 * q[iw, nb - 1]))
+            lim.append(8000.0)
+        p0.append(w.p_bh)
+    st = fim.Stepper(grid)
+    c = ocp.well_controls(ctrl, lim, dev)
+    st.step_wells(un, fn, 1.0, T(p0), c)                       # warm-up
+    c = ocp.well_controls(ctrl, lim, dev)
+    st.newton_iters = st.linear_iters = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    u, f, p, lins = st.step_wells(un, fn, 1.0, T(p0), c)
+    torch.cuda.synchronize(dev)
+    step_s = time.perf_counter() - t0
+    # the converged well equations: rate targets met
+    out = grid.linearize_wells(u, f, un, fn, 1.0, p, c)
+    nrm = grid.residual_norms(out["residual"], 1.0, out["well_res"], c).cpu().tolist()
+    # linearisation with and without the well rows, same state
+    stream = torch.cuda.current_stream(dev)
+    r = torch.empty(nb * grid.N, dtype=torch.float64, device=dev)
+    v = torch.empty(grid.nnzb * nb * nb, dtype=torch.float64, device=dev)
+    times = {}
+    for name, fn_ in (("linearize_ms", lambda: grid.linearize(u, f, un, fn, 1.0, r, v)),
+                      ("linearize_wells_ms", lambda: grid.linearize_wells(u, f, un, fn, 1.0, p, c, out=out))):
+        for _ in range(3):
+            fn_()
+        e0, e1 = _events(stream)
+        e0.record(stream)
+        for _ in range(reps):
+            fn_()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times[name] = e0.elapsed_time(e1) / reps
+    res = {"workload": "layered black-oil box 100x100x20, 5 rate-controlled wells, one step of 1 day",
+           "newton_iterations": st.newton_iters, "linearisations": lins, "linear_iterations": st.linear_iters,
+           "step_s": step_s, "ms_per_newton_iteration": 1e3 * step_s / max(st.newton_iters, 1),
+           "p_bh": p.cpu().tolist(), "controls_after": [list(x) for x in ocp.read_controls(c)],
+           "final_norms": nrm, "device_status": grid.status()}
+    res.update(times)
+    res["well_rows_overhead_ms"] = times["linearize_wells_ms"] - times["linearize_ms"]
+    return res
+
+
 def run_coupling(dev, local_rank, reps=20, with_oracle=False):
     """Adaptive subdomain coupling (Sec. 4) on the 4000x4000x1 flood (16
     million cells) split into 40x25 boxes: mark cells whose saturations moved
@@ -674,19 +741,25 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-model batched-ensemble measurement")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 300-cell, oil-water and history-match measurements")
-    ap.add_argument("--coupling-only", action="store_true",
-                    help="only the adaptive-coupling measurement, printed as one JSON line")
+    ap.add_argument("--only", choices=["coupling", "wells", "small_case", "oil_water", "adjoint", "ensemble"],
+                    help="only that side measurement, printed as one JSON line")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, no CPU baseline): the command profiled by ncu")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local_rank = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
-    if args.coupling_only:
+    if args.only:
         import torch
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)
-        print(json.dumps({"coupling": run_coupling(dev, local_rank, with_oracle=not args.no_cpu_baseline)}))
+        part = {"coupling": lambda: run_coupling(dev, local_rank, with_oracle=not args.no_cpu_baseline),
+                "wells": lambda: run_wells(dev, local_rank),
+                "small_case": lambda: run_small_case(dev, local_rank),
+                "oil_water": lambda: run_oil_water(dev, local_rank),
+                "adjoint": lambda: run_adjoint(dev, local_rank),
+                "ensemble": lambda: run_ensemble(dev, local_rank)}[args.only]
+        print(json.dumps({args.only: part()}))
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
