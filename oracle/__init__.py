@@ -17,7 +17,11 @@ Contents:
                  (used by the Buckley-Leverett pin and the gradient checks);
 * ``adjoint``    multi-step simulation and its discrete-adjoint gradient;
 * ``coupling``   the adaptive subdomain coupling of Sec. 4 (marked cells,
-                 coupling graph, connected components).
+                 coupling graph, connected components);
+* ``pn``         the equations in pressure and component amounts with the
+                 volume balance (Sec. 2.1, eq. 4), its explicit black-oil
+                 phase split, the elimination of the volume rows, and a
+                 Newton step in those unknowns.
 
 Parity status of each function is listed in the design notes; all of them are
 pinned by the CPU tests (``tests/test_oracle_*.py``).

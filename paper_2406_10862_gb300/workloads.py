@@ -129,11 +129,13 @@ def make_grid(nx, ny, nz, lnk, phi, wells, nphase=3, dx=300.0, dy=300.0, dz=30.0
 
 # ----------------------------------------------------------------- states
 def perturbed_state(g: GridDesc, rng, p0=4800.0, sw0=0.12, dt=1.0, frac_unsat=0.0,
-                    dp_sd=20.0, ds_hi=0.02):
+                    dp_sd=20.0, ds_hi=0.02, rs_hi=0.9):
     """Old state uniform (p0, sw0, S_g = 0, saturated); new state the old one
     plus a seeded perturbation, so that every flux and derivative is
     non-trivial.  A fraction ``frac_unsat`` of cells is flagged
-    undersaturated in both states, with X = R_s drawn inside the table range."""
+    undersaturated in both states, with X = R_s drawn as U(0.3, rs_hi) times
+    the table's largest R_s (rs_hi = 0.7 keeps it below the saturated R_s of
+    the table at p0 = 4800 psi, a consistent undersaturated oil)."""
     N, nv = g.N, g.nphase
     u_old = np.zeros((nv, N))
     u_old[0] = p0
@@ -143,7 +145,7 @@ def perturbed_state(g: GridDesc, rng, p0=4800.0, sw0=0.12, dt=1.0, frac_unsat=0.
         unsat = rng.random(N) < frac_unsat
         flag[unsat] = 1
         rs_max = float(np.max(g.tab_Rs))
-        u_old[2, unsat] = rng.uniform(0.3, 0.9, unsat.sum()) * rs_max
+        u_old[2, unsat] = rng.uniform(0.3, rs_hi, unsat.sum()) * rs_max
     u_new = u_old.copy()
     u_new[0] += rng.normal(0.0, dp_sd, N)
     u_new[1] += rng.uniform(0.0, ds_hi, N)
@@ -252,7 +254,7 @@ def ensemble(n_models=64, seed=4, lo=2e4, hi=4e5):
     return out
 
 
-def tiny(nx, ny, nz, nphase=3, seed=0, frac_unsat=0.3, wells=True, **over):
+def tiny(nx, ny, nz, nphase=3, seed=0, frac_unsat=0.3, wells=True, rs_hi=0.9, **over):
     """Small random grid for parity and edge-case tests: random ln k and phi,
     a producer and (three-phase: gas, two-phase: water) injector when the grid
     has at least two columns, mixed saturated/undersaturated cells."""
@@ -266,7 +268,7 @@ def tiny(nx, ny, nz, nphase=3, seed=0, frac_unsat=0.3, wells=True, **over):
         if nx * ny > 1:
             g.wells.append(Well(kind=1, phase=2 if nphase == 3 else 0, p_bh=5100.0,
                                 cells=g.column(0, 0)))
-    return g, perturbed_state(g, rng, frac_unsat=frac_unsat if nphase == 3 else 0.0)
+    return g, perturbed_state(g, rng, frac_unsat=frac_unsat if nphase == 3 else 0.0, rs_hi=rs_hi)
 
 
 def history_match(nx=100, ny=100, nz=10, seed_truth=51, seed_prior=52, seed_rock=5, nsteps=20, dt=1.0):
