@@ -354,6 +354,45 @@ ocp_status ocp_well_update(ocp_grid* grid, double* p_bh, const double* dp, doubl
 ocp_status ocp_residual_norms(ocp_grid* grid, const double* residual, double dt, const double* well_res,
                               const ocp_well_ctrl* ctrl, double* norms, void* cuda_stream);
 
+/* ---------------------------------------------------------------- pressure and amounts
+ * The paper's own unknowns (Sec. 2.1, eq. 4): per cell the pressure P and the
+ * component amounts N_w, N_o[, N_g] in surface volumes per bulk volume,
+ * variable-major [(nb+1)*N] (P, then N_w, ...).  The black-oil phase split is
+ * explicit: V_w = N_w / b_w; all gas dissolved (R_s = N_g / N_o,
+ * undersaturated oil) when N_g <= R_s,sat(P) N_o, else R_s = R_s,sat(P) and
+ * free gas V_g = (N_g - R_s N_o) / b_g; S_j = V_j / V_f.  Equations: the
+ * component balances (accumulation (N - N_old) V / dt, fluxes and fixed-BHP
+ * wells as ocp_linearize) and the volume balance r_v = phi(P) - V_f. */
+
+/* Linearises in (P, N) and eliminates N_w with every cell's volume-balance
+ * row (Schur complement on the diagonal block).  Writes the reduced system
+ * over (P, N_o[, N_g]): residual [nb*N] and bsr_val [nnzb*nb*nb] (the grid's
+ * pattern, block-interleaved as for ocp_linearize), and elim [(nb+1)*N]
+ * variable-major (c_P, c_o[, c_g], c_r) with which the N_w part of the
+ * solution x of the full system is x_Nw = c_r - c_P x_P - c_o x_No [- c_g x_Ng].
+ * With residual_full [(nb+1)*N] and/or bsr_val_full [nnzb*(nb+1)^2] (each
+ * may be NULL) also the full system, rows water, oil[, gas], volume and
+ * columns P, N_w, N_o[, N_g].  flag (device int8 [N], may be NULL) receives the
+ * split's state (1: undersaturated).  The first call on a grid allocates the
+ * split's per-cell data (32 doubles and a byte per cell with three phases, 18
+ * and a byte with two), so it must not be the call captured into a CUDA
+ * graph; later calls allocate nothing.  A non-finite input sets the sticky status OCP_ERR_NONFINITE. */
+ocp_status ocp_linearize_pn(ocp_grid* grid, const double* pn_new, const double* pn_old, double dt,
+                            double* residual, double* bsr_val, double* elim, double* residual_full,
+                            double* bsr_val_full, int8_t* flag, void* cuda_stream);
+
+/* pn += scale * x_full, where x_full is the solution of the full system built
+ * from the reduced solution dx [nb*N] (block-interleaved P, N_o[, N_g]) and
+ * elim.  dx_max (device, nb+1 doubles) receives max |scale x_full| per
+ * unknown (P, N_w, N_o[, N_g]). */
+ocp_status ocp_pn_update(ocp_grid* grid, double* pn, const double* dx, double scale, const double* elim,
+                         double* dx_max, void* cuda_stream);
+
+/* Convergence measures of the full (P, N) residual: norms[e] = max over cells
+ * of |R_e| / (phi V / dt) for the component rows e < nb, norms[3] = max |r_v|
+ * (device, 4 doubles). */
+ocp_status ocp_pn_norms(ocp_grid* grid, const double* residual_full, double dt, double* norms, void* cuda_stream);
+
 /* ---------------------------------------------------------------- adaptive coupling
  * The adaptively coupled domain decomposition of Sec. 4 decides at the start
  * of each time step which subdomains to solve together: (1) mark the cells

@@ -57,6 +57,8 @@ void free_grid(ocp_grid* g) {
   cudaFree(g->d_well_first);
   cudaFree(g->d_status);
   cudaFree(g->d_scratch);
+  cudaFree(g->d_pn);
+  cudaFree(g->d_pn_flag);
   delete g;
 }
 

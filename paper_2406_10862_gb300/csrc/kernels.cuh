@@ -7,7 +7,8 @@ namespace ocp {
 int64_t linearize_scratch_doubles(int64_t N);
 cudaError_t launch_linearize(const ocp_grid* g, const double* u_new, const int8_t* f_new,
                              const double* u_old, const int8_t* f_old, double dt, double* res,
-                             double* val, double* face_flux, cudaStream_t s, const double* p_bh = nullptr);
+                             double* val, double* face_flux, cudaStream_t s, const double* p_bh = nullptr,
+                             int no_acc = 0);
 // The same launches with the per-cell scratch given explicitly (used by the
 // entry point that must not allocate).
 cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const double* u_new,

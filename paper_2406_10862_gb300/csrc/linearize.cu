@@ -81,15 +81,20 @@ __device__ __forceinline__ void cell_body(const ModelArgs& M, const Table& T, lo
   CellQ q{};
   CellAux a{};
   cell_quantities<NB, true>(P, T, pn, swn, xn, fn & 1, phs, q, a, inj);
-  double mo[3];
-  cell_masses<NB, false>(P, T, po, swo, xo, fo & 1, phs, mo);
   double r[3], dg[3][3];
+  if (!M.no_acc) {
+    double mo[3];
+    cell_masses<NB, false>(P, T, po, swo, xo, fo & 1, phs, mo);
 #pragma unroll
-  for (int e = 0; e < NB; ++e) {
-    r[e] = a.m[e] - mo[e];
-    dg[e][0] = a.m_p[e];
-    dg[e][1] = a.m_sw[e];
-    dg[e][2] = a.m_x[e];
+    for (int e = 0; e < NB; ++e) {
+      r[e] = a.m[e] - mo[e];
+      dg[e][0] = a.m_p[e];
+      dg[e][1] = a.m_sw[e];
+      dg[e][2] = a.m_x[e];
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < NB; ++e) r[e] = dg[e][0] = dg[e][1] = dg[e][2] = 0.0;
   }
   if (ip >= 0) {
     double src[3], ds[3][3];
@@ -334,6 +339,7 @@ ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, co
   M.face_flux = face_flux;
   M.scale = g->prm.vol_rb / dt;
   M.p_bh = nullptr;
+  M.no_acc = 0;
   return M;
 }
 
@@ -341,9 +347,10 @@ namespace {
 
 cudaError_t launch_single(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
                           const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
-                          double* face_flux, cudaStream_t s, const double* p_bh = nullptr) {
+                          double* face_flux, cudaStream_t s, const double* p_bh = nullptr, int no_acc = 0) {
   ModelArgs M = model_args(g, scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux);
   M.p_bh = p_bh;
+  M.no_acc = no_acc;
   TileList lists[2];
   lists[0].models = nullptr;
   lists[0].tiles = nullptr;
@@ -360,8 +367,8 @@ int64_t linearize_scratch_doubles(int64_t N) { return (int64_t)100 * N; }
 
 cudaError_t launch_linearize(const ocp_grid* g, const double* u_new, const int8_t* f_new,
                              const double* u_old, const int8_t* f_old, double dt, double* res,
-                             double* val, double* face_flux, cudaStream_t s, const double* p_bh) {
-  return launch_single(g, g->d_scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s, p_bh);
+                             double* val, double* face_flux, cudaStream_t s, const double* p_bh, int no_acc) {
+  return launch_single(g, g->d_scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux, s, p_bh, no_acc);
 }
 
 cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const double* u_new,

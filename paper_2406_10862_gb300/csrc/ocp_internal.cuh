@@ -102,6 +102,8 @@ struct ocp_grid {
   int32_t* d_well_first;     // [nwell+1] perforations of well w: well_first[w] .. well_first[w+1]
   int* d_status;             // sticky device status word
   double* d_scratch;         // per-cell scratch of the linearisation
+  double* d_pn;              // per-cell data of the (P, N) path, allocated on its first use
+  int8_t* d_pn_flag;
   int64_t scratch_doubles;
   ocp::LaunchCfg cfg;        // launch shape of the linearisation
   int sms;                   // SM count of the device
@@ -130,6 +132,7 @@ struct ModelArgs {
   double* face_flux;
   double scale;              // bulk volume in rb / dt
   const double* p_bh;        // per-well bottom-hole pressures, or null for each perforation's own
+  int no_acc;                // 1: leave the accumulation out (the (P, N) path adds its own)
 };
 
 // Tiles of `TPB` consecutive cells: with models == nullptr the single model

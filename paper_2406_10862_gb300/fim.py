@@ -7,7 +7,9 @@ reverse pass of a loss on the well rates.  ``Stepper.step_wells`` runs the
 same iteration with the wells' bottom-hole pressures as unknowns under
 pressure or rate control (``ocp_linearize_wells``, ``ocp_bicgstab_wells``,
 ``ocp_well_update``) and a residual-norm convergence test
-(``ocp_residual_norms``).  The gradient with respect to the
+(``ocp_residual_norms``); ``Stepper.step_pn`` runs it in the paper's own
+unknowns, pressure and component amounts with the volume balance
+(``ocp_linearize_pn``, ``ocp_pn_update``, ``ocp_pn_norms``).  The gradient with respect to the
 log-permeability field is
 
     dL/d ln k = sum_n [ dl_n/d ln k - lambda_n^T dR_n/d ln k ],
@@ -47,6 +49,7 @@ class NewtonOptions:
     ds_max: float = 0.2
     tol_cnv: float = 1e-9        # scaled residual, per pore volume (with well unknowns)
     tol_well: float = 1e-9       # well residual, relative to the rate target (psi under pressure control)
+    tol_vol: float = 1e-12       # volume-balance residual, (P, N) unknowns
 
 
 class Stepper:
@@ -125,6 +128,34 @@ class Stepper:
             g.well_update(p, self._dp, -1.0, ctrl, self._dpmax, self._nsw_w)
             self.newton_iters += 1
             nsw = int(self.nsw.item()) + int(self._nsw_w.item())
+        raise NewtonFailure("Newton did not converge in %d iterations" % o.max_newton)
+
+    def step_pn(self, pn_old, dt, pn_start=None):
+        """One step in the (P, N) unknowns (Sec. 2.1): linearise and eliminate
+        the volume rows (``ocp_linearize_pn``), solve the reduced system,
+        recover N_w and update (``ocp_pn_update``).  Converged when the scaled
+        component residuals are below tol_cnv and the volume residuals below
+        tol_vol (``ocp_pn_norms``).  Returns (pn, flag, linearisations)."""
+        g, o = self.g, self.o
+        nb, N = g.nb, g.N
+        pn = (pn_old if pn_start is None else pn_start).clone()
+        if not hasattr(self, "_pnb"):
+            self._pnb = {"residual": self.r, "bsr_val": self.val, "residual_full": g.empty((nb + 1) * N)}
+            self._pn_norms = g.empty(4)
+            self._pn_dmax = g.empty(nb + 1)
+        for it in range(1, o.max_newton + 1):
+            b = self._pnb = g.linearize_pn(pn, pn_old, dt, out=self._pnb)
+            nrm = g.pn_norms(b["residual_full"], dt, self._pn_norms).cpu().tolist()
+            if max(nrm[:nb]) < o.tol_cnv and nrm[3] < o.tol_vol:
+                st = g.status()
+                if st != 0:
+                    raise NewtonFailure("device status %d" % st)
+                return pn, b["flag"].clone(), it
+            self.du.zero_()
+            _, li, _ = g.bicgstab(b["bsr_val"], b["residual"], self.du, o.rtol, o.maxit, work=self.work)
+            self.linear_iters += li
+            g.pn_update(pn, self.du, -1.0, b["elim"], self._pn_dmax)
+            self.newton_iters += 1
         raise NewtonFailure("Newton did not converge in %d iterations" % o.max_newton)
 
     def linearize_at(self, u, f, u_old, f_old, dt):

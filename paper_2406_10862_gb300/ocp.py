@@ -31,7 +31,8 @@ EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_patt
            "ocp_batch_set_shape", "ocp_batch_get_shape", "ocp_batch_get_status", "ocp_grid_set_shape",
            "ocp_solver_work_doubles", "ocp_bicgstab", "ocp_newton_update", "ocp_well_rates_vjp",
            "ocp_grid_update_perm", "ocp_coupling_work_ints", "ocp_coupling_components", "ocp_linearize_wells",
-           "ocp_bicgstab_wells", "ocp_well_update", "ocp_residual_norms", "ocp_bsr_spmv", "ocp_adjoint_vjp",
+           "ocp_bicgstab_wells", "ocp_well_update", "ocp_residual_norms", "ocp_linearize_pn", "ocp_pn_update",
+           "ocp_pn_norms", "ocp_bsr_spmv", "ocp_adjoint_vjp",
            "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
 
 # ocp_well_ctrl: int32 mode, int32 phase, double target, double limit (24 bytes)
@@ -144,6 +145,9 @@ def load(build_if_missing: bool = False):
                                        ctypes.POINTER(ctypes.c_double), vp]
     lib.ocp_well_update.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp, vp]
     lib.ocp_residual_norms.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp, vp]
+    lib.ocp_linearize_pn.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]
+    lib.ocp_pn_update.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp]
+    lib.ocp_pn_norms.argtypes = [vp, vp, ctypes.c_double, vp, vp]
     lib.ocp_grid_update_perm.argtypes = [vp, vp, vp]
     lib.ocp_coupling_work_ints.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.ocp_coupling_work_ints.restype = ctypes.c_int64
@@ -425,6 +429,40 @@ class Grid:
         norms = norms if norms is not None else self.empty(4)
         _check(load().ocp_residual_norms(self._h, _ptr(residual), float(dt), _ptr(well_res), _ptr(ctrl),
                                          _ptr(norms), _stream(self.device, stream)))
+        return norms
+
+    # ------------------------------------------------------------ pressure and amounts
+    def linearize_pn(self, pn_new, pn_old, dt, out=None, full=False, stream=None):
+        """``ocp_linearize_pn``: the reduced system over (P, N_o[, N_g]) and
+        the elimination coefficients; with ``full`` also the system with the
+        volume rows.  Returns a dict (residual, bsr_val, elim, flag[,
+        residual_full, bsr_val_full])."""
+        N, nb, L = self.N, self.nb, self.nb + 1
+        self._t(pn_new, L * N, torch.float64, "pn_new")
+        self._t(pn_old, L * N, torch.float64, "pn_old")
+        o = dict(out or {})
+        sizes = {"residual": nb * N, "bsr_val": self.nnzb * nb * nb, "elim": L * N}
+        if full:
+            sizes.update(residual_full=L * N, bsr_val_full=self.nnzb * L * L)
+        for k, n in sizes.items():
+            if o.get(k) is None:
+                o[k] = self.empty(n)
+            self._t(o[k], n, torch.float64, k)
+        if o.get("flag") is None:
+            o["flag"] = torch.empty(N, dtype=torch.int8, device=self.device)
+        self._t(o["flag"], N, torch.int8, "flag")
+        _check(load().ocp_linearize_pn(self._h, _ptr(pn_new), _ptr(pn_old), float(dt), _ptr(o["residual"]),
+                                       _ptr(o["bsr_val"]), _ptr(o["elim"]), _ptr(o.get("residual_full")),
+                                       _ptr(o.get("bsr_val_full")), _ptr(o["flag"]), _stream(self.device, stream)))
+        return o
+
+    def pn_update(self, pn, dx, scale, elim, dx_max, stream=None):
+        _check(load().ocp_pn_update(self._h, _ptr(pn), _ptr(dx), float(scale), _ptr(elim), _ptr(dx_max),
+                                    _stream(self.device, stream)))
+
+    def pn_norms(self, residual_full, dt, norms=None, stream=None):
+        norms = norms if norms is not None else self.empty(4)
+        _check(load().ocp_pn_norms(self._h, _ptr(residual_full), float(dt), _ptr(norms), _stream(self.device, stream)))
         return norms
 
     def coupling_components(self, u_new, flag_new, u_old, flag_old, threshold, px, py, pz, labels=None,
