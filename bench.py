@@ -375,6 +375,7 @@ def run_gpu(args, rank, world, local_rank):
             line["oil_water"] = run_oil_water(dev, local_rank)
             line["adjoint"] = run_adjoint(dev, local_rank)
             line["wells"] = run_wells(dev, local_rank)
+            line["pn"] = run_pn(dev, local_rank)
             line["coupling"] = run_coupling(dev, local_rank, with_oracle=(world == 1 and not args.no_cpu_baseline))
         if world == 1 and not args.no_cpu_baseline:
             t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s)
@@ -606,6 +607,61 @@ def run_wells(dev, local_rank, reps=20):
     return res
 
 
+def run_pn(dev, local_rank, reps=20):
+    """The 200 000-cell box in the paper's own unknowns, pressure and
+    component amounts with the volume balance: one linearisation with the
+    volume rows eliminated (3x3 blocks), the same with the full 4x4 system
+    written too, and the natural-variable linearisation of the same state;
+    then one backward-Euler step of 1 day by Newton in (P, N)."""
+    import numpy as np
+    import torch
+
+    from paper_2406_10862_gb300 import fim, ocp, workloads as W
+
+    g, s = W.layered_box()
+    grid = ocp.Grid(g, local_rank)
+    nb, N = grid.nb, grid.N
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    un, fn, uo, fo = T(s.u_new.ravel()), T(s.flag_new), T(s.u_old.ravel()), T(s.flag_old)
+    pn_new, pn_old = grid.pn_from_natural(un, fn), grid.pn_from_natural(uo, fo)
+    r = torch.empty(nb * N, dtype=torch.float64, device=dev)
+    v = torch.empty(grid.nnzb * nb * nb, dtype=torch.float64, device=dev)
+    red = grid.linearize_pn(pn_new, pn_old, 1.0)
+    full = grid.linearize_pn(pn_new, pn_old, 1.0, full=True)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 2 ** 20 // 8, dtype=torch.float64, device=dev)
+    times = {}
+    for name, fn_ in (("natural_linearize_ms", lambda: grid.linearize(un, fn, uo, fo, 1.0, r, v)),
+                      ("pn_linearize_ms", lambda: grid.linearize_pn(pn_new, pn_old, 1.0, out=red)),
+                      ("pn_linearize_full_ms", lambda: grid.linearize_pn(pn_new, pn_old, 1.0, out=full, full=True))):
+        for _ in range(3):
+            fn_()
+        tot = 0.0
+        for k in range(reps):
+            flush.fill_(float(k))
+            e0, e1 = _events(stream)
+            e0.record(stream)
+            fn_()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            tot += e0.elapsed_time(e1)
+        times[name] = tot / reps
+    st = fim.Stepper(grid)
+    st.step_pn(pn_old, 1.0)                                   # warm-up
+    st.newton_iters = st.linear_iters = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    pn, flag, lins = st.step_pn(pn_old, 1.0)
+    torch.cuda.synchronize(dev)
+    out = {"workload": "layered black-oil box 100x100x20 in (P, N_w, N_o, N_g), volume rows eliminated",
+           "cells": N, "mcells_per_s_reduced": N / (times["pn_linearize_ms"] * 1e-3) / 1e6,
+           "newton_iterations": st.newton_iters, "linearisations": lins, "linear_iterations": st.linear_iters,
+           "step_s": time.perf_counter() - t0, "device_status": grid.status(),
+           "l2": "flushed before every timed linearisation"}
+    out.update(times)
+    return out
+
+
 def run_coupling(dev, local_rank, reps=20, with_oracle=False):
     """Adaptive subdomain coupling (Sec. 4) on the 4000x4000x1 flood (16
     million cells) split into 40x25 boxes: mark cells whose saturations moved
@@ -741,7 +797,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-model batched-ensemble measurement")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 300-cell, oil-water and history-match measurements")
-    ap.add_argument("--only", choices=["coupling", "wells", "small_case", "oil_water", "adjoint", "ensemble"],
+    ap.add_argument("--only", choices=["coupling", "wells", "pn", "small_case", "oil_water", "adjoint", "ensemble"],
                     help="only that side measurement, printed as one JSON line")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, no CPU baseline): the command profiled by ncu")
@@ -755,6 +811,7 @@ def main():
         torch.cuda.set_device(dev)
         part = {"coupling": lambda: run_coupling(dev, local_rank, with_oracle=not args.no_cpu_baseline),
                 "wells": lambda: run_wells(dev, local_rank),
+                "pn": lambda: run_pn(dev, local_rank),
                 "small_case": lambda: run_small_case(dev, local_rank),
                 "oil_water": lambda: run_oil_water(dev, local_rank),
                 "adjoint": lambda: run_adjoint(dev, local_rank),

@@ -388,6 +388,11 @@ ocp_status ocp_linearize_pn(ocp_grid* grid, const double* pn_new, const double* 
 ocp_status ocp_pn_update(ocp_grid* grid, double* pn, const double* dx, double scale, const double* elim,
                          double* dx_max, void* cuda_stream);
 
+/* (P, N) [(nb+1)*N] of a natural state u, flag (as for ocp_linearize):
+ * P = p and N = phi(p) S b per bulk volume (eq. 4), on the volume-balance
+ * manifold. */
+ocp_status ocp_pn_from_natural(ocp_grid* grid, const double* u, const int8_t* flag, double* pn, void* cuda_stream);
+
 /* Convergence measures of the full (P, N) residual: norms[e] = max over cells
  * of |R_e| / (phi V / dt) for the component rows e < nb, norms[3] = max |r_v|
  * (device, 4 doubles). */

@@ -239,6 +239,21 @@ __global__ void pn_norm_kernel(long long N, const double* __restrict__ phi, doub
   atomicMax(&out[3], (unsigned long long)__double_as_longlong(fabs(res4[c * L + NB])));
 }
 
+// (P, N) of a natural state: N = phi S b per bulk volume (eq. 4)
+template <int NB>
+__global__ void pn_from_natural_kernel(Params P, const Table* __restrict__ gT, const double* __restrict__ u,
+                                       const int8_t* __restrict__ flag, const double* __restrict__ phi_ref,
+                                       double* __restrict__ pn) {
+  const long long N = P.N;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  double m[3];
+  cell_masses<NB, false>(P, *gT, u[c], u[N + c], NB == 3 ? u[2 * N + c] : 0.0, NB == 3 ? (flag[c] & 1) : 0,
+                         phi_ref[c], m);
+  pn[c] = u[c];
+  for (int e = 0; e < NB; ++e) pn[(e + 1) * N + c] = m[e];
+}
+
 unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 struct Guard {
@@ -329,6 +344,20 @@ ocp_status ocp_pn_update(ocp_grid* g, double* pn, const double* dx, double scale
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_pn_update: %s", cudaGetErrorString(e));
+  return OCP_OK;
+}
+
+ocp_status ocp_pn_from_natural(ocp_grid* g, const double* u, const int8_t* flag, double* pn, void* stream) {
+  using namespace ocp;
+  if (!g || !u || !pn || (g->prm.nb == 3 && !flag)) return report(OCP_ERR_INVALID_ARG, "grid, u, flag and pn are required");
+  Guard guard(g->device);
+  if (guard.err != cudaSuccess) return report(OCP_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(guard.err));
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long N = g->prm.N;
+  if (g->prm.nb == 3) pn_from_natural_kernel<3><<<nblk(N), 256, 0, s>>>(g->prm, g->d_table, u, flag, g->d_phi, pn);
+  else pn_from_natural_kernel<2><<<nblk(N), 256, 0, s>>>(g->prm, g->d_table, u, flag, g->d_phi, pn);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_pn_from_natural: %s", cudaGetErrorString(e));
   return OCP_OK;
 }
 

@@ -32,7 +32,7 @@ EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_patt
            "ocp_solver_work_doubles", "ocp_bicgstab", "ocp_newton_update", "ocp_well_rates_vjp",
            "ocp_grid_update_perm", "ocp_coupling_work_ints", "ocp_coupling_components", "ocp_linearize_wells",
            "ocp_bicgstab_wells", "ocp_well_update", "ocp_residual_norms", "ocp_linearize_pn", "ocp_pn_update",
-           "ocp_pn_norms", "ocp_bsr_spmv", "ocp_adjoint_vjp",
+           "ocp_pn_norms", "ocp_pn_from_natural", "ocp_bsr_spmv", "ocp_adjoint_vjp",
            "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
 
 # ocp_well_ctrl: int32 mode, int32 phase, double target, double limit (24 bytes)
@@ -148,6 +148,7 @@ def load(build_if_missing: bool = False):
     lib.ocp_linearize_pn.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]
     lib.ocp_pn_update.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp]
     lib.ocp_pn_norms.argtypes = [vp, vp, ctypes.c_double, vp, vp]
+    lib.ocp_pn_from_natural.argtypes = [vp, vp, vp, vp, vp]
     lib.ocp_grid_update_perm.argtypes = [vp, vp, vp]
     lib.ocp_coupling_work_ints.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.ocp_coupling_work_ints.restype = ctypes.c_int64
@@ -459,6 +460,13 @@ class Grid:
     def pn_update(self, pn, dx, scale, elim, dx_max, stream=None):
         _check(load().ocp_pn_update(self._h, _ptr(pn), _ptr(dx), float(scale), _ptr(elim), _ptr(dx_max),
                                     _stream(self.device, stream)))
+
+    def pn_from_natural(self, u, flag, pn=None, stream=None):
+        """(P, N) of a natural state (``ocp_pn_from_natural``)."""
+        pn = pn if pn is not None else self.empty((self.nb + 1) * self.N)
+        self._t(u, self.nb * self.N, torch.float64, "u")
+        _check(load().ocp_pn_from_natural(self._h, _ptr(u), _ptr(flag), _ptr(pn), _stream(self.device, stream)))
+        return pn
 
     def pn_norms(self, residual_full, dt, norms=None, stream=None):
         norms = norms if norms is not None else self.empty(4)

@@ -90,3 +90,14 @@ def test_newton_step_pn_matches_oracle(nphase):
     for e in range(1, nphase + 1):
         assert np.allclose(got[e], ref[e], rtol=1e-10, atol=1e-14)
     assert abs(it - it_ref) <= 1
+
+
+@pytest.mark.parametrize("nphase", [2, 3])
+def test_pn_from_natural_matches_oracle(nphase):
+    need_gpu()
+    from paper_2406_10862_gb300 import ocp
+    g, s = W.tiny(7, 6, 4, nphase=nphase, seed=14, frac_unsat=0.3 if nphase == 3 else 0.0, rs_hi=0.7)
+    grid = ocp.Grid(g)
+    got = grid.pn_from_natural(_T(s.u_new.ravel()), _T(s.flag_new)).cpu().numpy().reshape(nphase + 1, g.N)
+    ref = natural_to_pn(g, s.u_new, s.flag_new)
+    assert np.allclose(got, ref, rtol=1e-14, atol=0.0)
