@@ -21,7 +21,10 @@ Contents:
 * ``pn``         the equations in pressure and component amounts with the
                  volume balance (Sec. 2.1, eq. 4), its explicit black-oil
                  phase split, the elimination of the volume rows, and a
-                 Newton step in those unknowns.
+                 Newton step in those unknowns;
+* ``impec``      one IMPEC step in those unknowns: the pressure equation
+                 from the linearised volume balance with coefficients frozen
+                 at the old level, its direct solve, and the explicit update.
 
 Parity status of each function is listed in the design notes; all of them are
 pinned by the CPU tests (``tests/test_oracle_*.py``).
