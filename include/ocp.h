@@ -398,6 +398,37 @@ ocp_status ocp_pn_from_natural(ocp_grid* grid, const double* u, const int8_t* fl
  * (device, 4 doubles). */
 ocp_status ocp_pn_norms(ocp_grid* grid, const double* residual_full, double dt, double* norms, void* cuda_stream);
 
+/* ---------------------------------------------------------------- IMPEC
+ * One IMPEC step (implicit pressure, explicit composition) in the (P, N)
+ * unknowns above: the volume balance at the new level, linearised about the
+ * old one and multiplied by V/dt,
+ *   (V/dt)(phi - V_f) + (V/dt)(phi' - V_f,P) dP + sum_i w_i (sum_faces F_i - Q_i) = 0,
+ * w_i = dV_f/dN_i, with every face's phase flux F = T lambda_up (Phi_i - Phi_j)
+ * linear in the new pressure (mobility, upwind side, density and capillary
+ * offset frozen at the old level; dissolved gas with the oil's upwind R_s) and
+ * the wells at the new cell pressure with old mobilities and open state; then
+ * N^{n+1} = N^n + (Q - sum F) dt / V at the new pressure. */
+
+/* Builds the pressure system A dP = rhs for the state pn [(nb+1)*N]: val
+ * [nnzb] one value per block of the grid's 7-point pattern (row order as
+ * ocp_bsr_pattern), rhs [N].  The old-level data are kept in the grid's
+ * linearisation scratch for ocp_impec_update: no other call that uses the
+ * grid's scratch (ocp_linearize, ocp_linearize_wells, ocp_linearize_pn) may
+ * come between the two on the grid. */
+ocp_status ocp_impec_pressure(ocp_grid* grid, const double* pn, double dt, double* val, double* rhs,
+                              void* cuda_stream);
+
+/* The explicit update after ocp_impec_pressure(pn_old, dt) and a solve for
+ * dp [N]: pn_new = (P + dp, N + (Q - sum F) dt / V).  pn_new must not
+ * overlap pn_old. */
+ocp_status ocp_impec_update(ocp_grid* grid, const double* pn_old, const double* dp, double dt, double* pn_new,
+                            void* cuda_stream);
+
+/* ocp_bicgstab for a scalar system on the grid's pattern (one value per
+ * block, e.g. the IMPEC pressure matrix), Jacobi preconditioned; b, x [N]. */
+ocp_status ocp_bicgstab_scalar(ocp_grid* grid, const double* val, const double* b, double* x, double rtol,
+                               int maxit, double* work, int* iters, double* relres, void* cuda_stream);
+
 /* ---------------------------------------------------------------- adaptive coupling
  * The adaptively coupled domain decomposition of Sec. 4 decides at the start
  * of each time step which subdomains to solve together: (1) mark the cells

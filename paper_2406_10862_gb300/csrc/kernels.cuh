@@ -33,16 +33,18 @@ cudaError_t launch_well_schur(const ocp_grid* g, const WellSchur& ws, int mode, 
                               double* out, const double* bw, double* xw, cudaStream_t s);
 // Left block-Jacobi BiCGSTAB on A (ws == nullptr) or on the Schur complement
 // A - bs d^-1 cs of the well unknowns.
+// nbs: block size of the system (0: the grid's; 1: a scalar system on the
+// grid's pattern).
 ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, const double* b, double* x,
                         double rtol, int maxit, int transpose, double* work, int* iters, double* relres,
-                        cudaStream_t s);
+                        cudaStream_t s, int nbs = 0);
 cudaError_t launch_tiles(int nb, const TileList* lists, const ModelArgs& single, const LaunchCfg& cfg,
                          int sms, cudaStream_t s);
 ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
                      const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
                      double* face_flux);
 cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, const double* x, double beta,
-                        double* y, int transpose, cudaStream_t s);
+                        double* y, int transpose, cudaStream_t s, int nbs = 0);
 cudaError_t launch_vjp(const ocp_grid* g, const double* u_new, const int8_t* f_new, const double* u_old,
                        const int8_t* f_old, double dt, const double* val, const double* face_flux,
                        const double* lam, double* g_unew, double* g_uold, double* g_lnk, double* g_phi,

@@ -123,7 +123,10 @@ __global__ void block_jacobi_kernel(Params P, const int32_t* __restrict__ row_pt
     }
   }
   double det;
-  if (NB == 3) {
+  if constexpr (NB == 1) {
+    det = a[0][0];
+    inv[0][0] = 1.0 / det;
+  } else if constexpr (NB == 3) {
     const double c00 = a[1][1] * a[2][2] - a[1][2] * a[2][1];
     const double c01 = a[1][2] * a[2][0] - a[1][0] * a[2][2];
     const double c02 = a[1][0] * a[2][1] - a[1][1] * a[2][0];
@@ -268,9 +271,9 @@ int64_t solver_work_doubles(const ocp_grid* g) {
 
 ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, const double* b, double* x,
                         double rtol, int maxit, int transpose, double* work, int* iters, double* relres,
-                        cudaStream_t s) {
+                        cudaStream_t s, int nbs) {
   if (!(rtol > 0.0) || maxit < 1) return report(OCP_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 1");
-  const int nb = g->prm.nb;
+  const int nb = nbs > 0 ? nbs : g->prm.nb;
   const long long N = g->prm.N, n = nb * N;
   double* r = work;
   double* r0 = r + n;
@@ -290,19 +293,23 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
   };
   auto apply = [&](const double* in, double* out) {
     if (nb == 3) bj_apply_kernel<3><<<bc, 256, 0, s>>>(N, dinv, in, out);
-    else bj_apply_kernel<2><<<bc, 256, 0, s>>>(N, dinv, in, out);
+    else if (nb == 2) bj_apply_kernel<2><<<bc, 256, 0, s>>>(N, dinv, in, out);
+    else bj_apply_kernel<1><<<bc, 256, 0, s>>>(N, dinv, in, out);
   };
   cudaError_t e = cudaSuccess;
   const WellSchur wsv = ws ? *ws : WellSchur{nullptr, nullptr, nullptr};
   if (nb == 3)
     block_jacobi_kernel<3><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status,
                                               g->d_perf_of_cell, g->d_perf, wsv);
-  else
+  else if (nb == 2)
     block_jacobi_kernel<2><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status,
+                                              g->d_perf_of_cell, g->d_perf, wsv);
+  else
+    block_jacobi_kernel<1><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status,
                                               g->d_perf_of_cell, g->d_perf, wsv);
   // the operator: A, or A - bs d^-1 cs with well terms
   auto op = [&](const double* in, double* out) {
-    cudaError_t err = launch_spmv(g, val, 1.0, in, 0.0, out, transpose, s);
+    cudaError_t err = launch_spmv(g, val, 1.0, in, 0.0, out, transpose, s, nb);
     if (err == cudaSuccess && ws) err = launch_well_schur(g, *ws, 0, -1.0, in, out, nullptr, nullptr, s);
     return err;
   };
@@ -312,7 +319,7 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
   // y = D^-1 b and r = D^-1 (b - A x)
   apply(b, y);
   if (e == cudaSuccess) e = cudaMemcpyAsync(t, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = launch_spmv(g, val, -1.0, x, 1.0, t, transpose, s);
+  if (e == cudaSuccess) e = launch_spmv(g, val, -1.0, x, 1.0, t, transpose, s, nb);
   if (e == cudaSuccess && ws) e = launch_well_schur(g, *ws, 0, 1.0, x, t, nullptr, nullptr, s);
   apply(t, r);
   if (e == cudaSuccess) e = cudaMemcpyAsync(r0, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);

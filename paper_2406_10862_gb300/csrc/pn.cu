@@ -25,6 +25,7 @@
 
 #include "kernels.cuh"
 #include "ocp_internal.cuh"
+#include "pn_split.cuh"
 
 namespace ocp {
 namespace {
@@ -52,65 +53,13 @@ __global__ void pn_split_kernel(Params P, const Table* __restrict__ gT, const do
   const Table& T = *gT;
   const double p = pn[c], nw = pn[N + c], no = pn[2 * N + c], ng = (NB == 3) ? pn[3 * N + c] : 0.0;
   if (!(finite(p) && finite(nw) && finite(no) && finite(ng))) atomicOr(status, kStatNonFinite);
-  int f = 0;
-  double x_pvt = 0.0;
-  if (NB == 3) {
-    Pvt s0;
-    pvt<3, false>(P, T, p, 0.0, 0, s0);           // R_s,sat(p)
-    if (positive(no) && ng <= s0.rs * no) {
-      f = 1;
-      x_pvt = ng / no;
-    }
-  }
-  Pvt v;
-  pvt<NB, false>(P, T, p, x_pvt, f, v);
-  // volumes per bulk volume and their derivatives by (P, N_w, N_o[, N_g])
-  double dVw[L] = {}, dVo[L] = {}, dVg[L] = {}, dRs[L] = {};
-  const double ibw = 1.0 / v.bw;
-  const double Vw = nw * ibw;
-  dVw[0] = -Vw * v.bw_p * ibw;
-  dVw[1] = ibw;
-  const double ibo = 1.0 / v.bo;
-  const double Vo = no * ibo;
-  double Vg = 0.0;
-  if (NB == 3 && f == 1) {
-    const double ino = 1.0 / no;
-    dRs[2] = -x_pvt * ino;
-    dRs[3] = ino;
-    dVo[0] = -Vo * v.bo_p * ibo;
-    dVo[2] = ibo - Vo * v.bo_x * dRs[2] * ibo;
-    dVo[3] = -Vo * v.bo_x * dRs[3] * ibo;
-  } else {
-    dVo[0] = -Vo * v.bo_p * ibo;
-    dVo[2] = ibo;
-    if (NB == 3) {
-      const double ibg = 1.0 / v.bg;
-      Vg = fma(-v.rs, no, ng) * ibg;
-      dVg[0] = fma(-v.rs_p, no, -Vg * v.bg_p) * ibg;
-      dVg[2] = -v.rs * ibg;
-      dVg[3] = ibg;
-    }
-  }
-  const double Vf = Vw + Vo + Vg;
-  const double iVf = 1.0 / Vf;
-  double dVf[L];
-  for (int k = 0; k < L; ++k) dVf[k] = dVw[k] + dVo[k] + dVg[k];
-  const double sw = Vw * iVf;
-  double M[NB][L];
-  for (int k = 0; k < L; ++k) {
-    M[0][k] = (k == 0) ? 1.0 : 0.0;
-    M[1][k] = (dVw[k] - sw * dVf[k]) * iVf;
-  }
-  double x = 0.0;
-  if (NB == 3) {
-    if (f == 1) {
-      x = x_pvt;
-      for (int k = 0; k < L; ++k) M[2][k] = dRs[k];
-    } else {
-      x = Vg * iVf;
-      for (int k = 0; k < L; ++k) M[2][k] = (dVg[k] - x * dVf[k]) * iVf;
-    }
-  }
+  Split<NB> sp;
+  phase_split<NB>(P, T, p, nw, no, ng, sp);
+  const double Vf = sp.Vf;
+  const double* dVf = sp.dVf;
+  const double sw = sp.sw, x = sp.x;
+  const int f = sp.flag;
+  const auto& M = sp.M;
   // volume balance r_v = phi(p) - V_f and its row a
   const double phi = phi_ref[c] * fma(P.cr, p - P.p_ref, 1.0);
   const double rv = phi - Vf;

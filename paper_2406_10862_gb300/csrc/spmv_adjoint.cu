@@ -333,17 +333,21 @@ cudaError_t launch_setup(ocp_grid* g, const double* d_lnk, double dx, double dy,
 }
 
 cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, const double* x, double beta,
-                        double* y, int transpose, cudaStream_t s) {
+                        double* y, int transpose, cudaStream_t s, int nbs) {
   const long long N = g->prm.N;
   const unsigned blocks = (unsigned)((N + 255) / 256);
   const int mode = (beta != 0.0) ? 2 : (alpha != 1.0 ? 1 : 0);
   const unsigned gblocks = (unsigned)((N + kSpmvThreads - 1) / kSpmvThreads);
-  if (g->prm.nb == 3) {
+  const int nb = nbs > 0 ? nbs : g->prm.nb;
+  if (nb == 3) {
     if (transpose) spmv_kernel<3, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
     else spmv_grid_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
-  } else {
+  } else if (nb == 2) {
     if (transpose) spmv_kernel<2, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
     else spmv_grid_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
+  } else {
+    if (transpose) spmv_kernel<1, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+    else spmv_grid_kernel<1><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
   }
   return cudaGetLastError();
 }

@@ -9,7 +9,8 @@ pressure or rate control (``ocp_linearize_wells``, ``ocp_bicgstab_wells``,
 ``ocp_well_update``) and a residual-norm convergence test
 (``ocp_residual_norms``); ``Stepper.step_pn`` runs it in the paper's own
 unknowns, pressure and component amounts with the volume balance
-(``ocp_linearize_pn``, ``ocp_pn_update``, ``ocp_pn_norms``).  The gradient with respect to the
+(``ocp_linearize_pn``, ``ocp_pn_update``, ``ocp_pn_norms``); ``impec_step``
+is one IMPEC step in the same unknowns.  The gradient with respect to the
 log-permeability field is
 
     dL/d ln k = sum_n [ dl_n/d ln k - lambda_n^T dR_n/d ln k ],
@@ -161,6 +162,17 @@ class Stepper:
     def linearize_at(self, u, f, u_old, f_old, dt):
         self.g.linearize(u, f, u_old, f_old, dt, self.r, self.val, self.ff)
         return self.r, self.val, self.ff
+
+
+def impec_step(grid, pn_old, dt, rtol=1e-13, maxit=2000, work=None):
+    """One IMPEC step in the (P, N) unknowns: the pressure system
+    (``ocp_impec_pressure``), its Jacobi-preconditioned BiCGSTAB solve
+    (``ocp_bicgstab_scalar``) and the explicit update (``ocp_impec_update``).
+    Returns (pn_new, dP, linear iterations)."""
+    val, rhs = grid.impec_pressure(pn_old, dt)
+    dp = torch.zeros(grid.N, dtype=torch.float64, device=grid.device)
+    _, it, _ = grid.bicgstab_scalar(val, rhs, dp, rtol, maxit, work=work)
+    return grid.impec_update(pn_old, dp, dt), dp, it
 
 
 def to_blocks(v, nb, N):

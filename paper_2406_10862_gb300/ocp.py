@@ -32,7 +32,7 @@ EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_patt
            "ocp_solver_work_doubles", "ocp_bicgstab", "ocp_newton_update", "ocp_well_rates_vjp",
            "ocp_grid_update_perm", "ocp_coupling_work_ints", "ocp_coupling_components", "ocp_linearize_wells",
            "ocp_bicgstab_wells", "ocp_well_update", "ocp_residual_norms", "ocp_linearize_pn", "ocp_pn_update",
-           "ocp_pn_norms", "ocp_pn_from_natural", "ocp_bsr_spmv", "ocp_adjoint_vjp",
+           "ocp_pn_norms", "ocp_pn_from_natural", "ocp_impec_pressure", "ocp_impec_update", "ocp_bicgstab_scalar", "ocp_bsr_spmv", "ocp_adjoint_vjp",
            "ocp_well_rates", "ocp_get_status", "ocp_last_error"]
 
 # ocp_well_ctrl: int32 mode, int32 phase, double target, double limit (24 bytes)
@@ -149,6 +149,10 @@ def load(build_if_missing: bool = False):
     lib.ocp_pn_update.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp]
     lib.ocp_pn_norms.argtypes = [vp, vp, ctypes.c_double, vp, vp]
     lib.ocp_pn_from_natural.argtypes = [vp, vp, vp, vp, vp]
+    lib.ocp_impec_pressure.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp]
+    lib.ocp_impec_update.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
+    lib.ocp_bicgstab_scalar.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp]
     lib.ocp_grid_update_perm.argtypes = [vp, vp, vp]
     lib.ocp_coupling_work_ints.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.ocp_coupling_work_ints.restype = ctypes.c_int64
@@ -467,6 +471,34 @@ class Grid:
         self._t(u, self.nb * self.N, torch.float64, "u")
         _check(load().ocp_pn_from_natural(self._h, _ptr(u), _ptr(flag), _ptr(pn), _stream(self.device, stream)))
         return pn
+
+    # ------------------------------------------------------------ IMPEC
+    def impec_pressure(self, pn, dt, val=None, rhs=None, stream=None):
+        """``ocp_impec_pressure``: (val [nnzb], rhs [N]) of the pressure system."""
+        self._t(pn, (self.nb + 1) * self.N, torch.float64, "pn")
+        val = val if val is not None else self.empty(self.nnzb)
+        rhs = rhs if rhs is not None else self.empty(self.N)
+        self._t(val, self.nnzb, torch.float64, "val")
+        self._t(rhs, self.N, torch.float64, "rhs")
+        _check(load().ocp_impec_pressure(self._h, _ptr(pn), float(dt), _ptr(val), _ptr(rhs),
+                                         _stream(self.device, stream)))
+        return val, rhs
+
+    def impec_update(self, pn_old, dp, dt, pn_new=None, stream=None):
+        pn_new = pn_new if pn_new is not None else self.empty((self.nb + 1) * self.N)
+        self._t(dp, self.N, torch.float64, "dp")
+        _check(load().ocp_impec_update(self._h, _ptr(pn_old), _ptr(dp), float(dt), _ptr(pn_new),
+                                       _stream(self.device, stream)))
+        return pn_new
+
+    def bicgstab_scalar(self, val, b, x, rtol, maxit, work=None, stream=None, check=True):
+        work = work if work is not None else self.solver_work()
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        st = load().ocp_bicgstab_scalar(self._h, _ptr(val), _ptr(b), _ptr(x), float(rtol), int(maxit), _ptr(work),
+                                        ctypes.byref(it), ctypes.byref(rr), _stream(self.device, stream))
+        if check:
+            _check(st)
+        return st, it.value, rr.value
 
     def pn_norms(self, residual_full, dt, norms=None, stream=None):
         norms = norms if norms is not None else self.empty(4)
