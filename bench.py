@@ -376,6 +376,7 @@ def run_gpu(args, rank, world, local_rank):
             line["adjoint"] = run_adjoint(dev, local_rank)
             line["wells"] = run_wells(dev, local_rank)
             line["pn"] = run_pn(dev, local_rank)
+            line["impec"] = run_impec(dev, local_rank)
             line["coupling"] = run_coupling(dev, local_rank, with_oracle=(world == 1 and not args.no_cpu_baseline))
         if world == 1 and not args.no_cpu_baseline:
             t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s)
@@ -662,6 +663,59 @@ def run_pn(dev, local_rank, reps=20):
     return out
 
 
+def run_impec(dev, local_rank, reps=20):
+    """IMPEC on the 200 000-cell box in (P, N): the pressure system
+    (ocp_impec_pressure), its Jacobi BiCGSTAB solve and the explicit update,
+    one step of 0.1 day from the perturbed state, timed part by part."""
+    import numpy as np
+    import torch
+
+    from paper_2406_10862_gb300 import fim, ocp, workloads as W
+
+    g, s = W.layered_box()
+    grid = ocp.Grid(g, local_rank)
+    N = grid.N
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    pn0 = grid.pn_from_natural(T(s.u_new.ravel()), T(s.flag_new))
+    dt = 0.1
+    work = grid.solver_work()
+    val, rhs = grid.impec_pressure(pn0, dt)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 2 ** 20 // 8, dtype=torch.float64, device=dev)
+    dp = torch.zeros(N, dtype=torch.float64, device=dev)
+    pn1 = grid.empty(4 * N)
+    times = {"pressure_system_ms": 0.0, "update_ms": 0.0}
+    for k in range(reps + 3):
+        flush.fill_(float(k))
+        e0, e1 = _events(stream)
+        e0.record(stream)
+        grid.impec_pressure(pn0, dt, val, rhs)
+        e1.record(stream)
+        dp.zero_()
+        grid.bicgstab_scalar(val, rhs, dp, 1e-12, 4000, work=work)
+        flush.fill_(float(k))
+        e2, e3 = _events(stream)
+        e2.record(stream)
+        grid.impec_update(pn0, dp, dt, pn1)
+        e3.record(stream)
+        torch.cuda.synchronize(dev)
+        if k >= 3:
+            times["pressure_system_ms"] += e0.elapsed_time(e1) / reps
+            times["update_ms"] += e2.elapsed_time(e3) / reps
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    _, dp2, its = fim.impec_step(grid, pn0, dt, rtol=1e-12, work=work)
+    torch.cuda.synchronize(dev)
+    step_s = time.perf_counter() - t0
+    x0, x1 = pn0.view(4, N), pn1.view(4, N)
+    out = {"workload": "layered black-oil box 100x100x20 in (P, N), one IMPEC step of 0.1 day", "cells": N,
+           "solve_iterations": its, "step_s": step_s, "max_dp_psi": float(dp2.abs().max()),
+           "max_dN": [float((x1[e] - x0[e]).abs().max()) for e in range(1, 4)],
+           "device_status": grid.status(), "l2": "flushed before each timed kernel sequence"}
+    out.update(times)
+    return out
+
+
 def run_coupling(dev, local_rank, reps=20, with_oracle=False):
     """Adaptive subdomain coupling (Sec. 4) on the 4000x4000x1 flood (16
     million cells) split into 40x25 boxes: mark cells whose saturations moved
@@ -797,7 +851,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-model batched-ensemble measurement")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 300-cell, oil-water and history-match measurements")
-    ap.add_argument("--only", choices=["coupling", "wells", "pn", "small_case", "oil_water", "adjoint", "ensemble"],
+    ap.add_argument("--only", choices=["coupling", "wells", "pn", "impec", "small_case", "oil_water", "adjoint", "ensemble"],
                     help="only that side measurement, printed as one JSON line")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, no CPU baseline): the command profiled by ncu")
@@ -812,6 +866,7 @@ def main():
         part = {"coupling": lambda: run_coupling(dev, local_rank, with_oracle=not args.no_cpu_baseline),
                 "wells": lambda: run_wells(dev, local_rank),
                 "pn": lambda: run_pn(dev, local_rank),
+                "impec": lambda: run_impec(dev, local_rank),
                 "small_case": lambda: run_small_case(dev, local_rank),
                 "oil_water": lambda: run_oil_water(dev, local_rank),
                 "adjoint": lambda: run_adjoint(dev, local_rank),
