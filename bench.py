@@ -169,6 +169,60 @@ def oracle_sample_times(g, s, sx=100, sy=100, sz=2, n_rows=2000, seed=9):
     return t_lin, t_spmv, t_vjp, desc
 
 
+def _oracle_slab_task(task):
+    """One process of the all-cores oracle baseline: the oracle linearisation
+    of one slab of the workload (its owned layers plus ghost layers).
+    Returns (owned cells, seconds)."""
+    rank, world = task
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from oracle.linearize import linearize
+    from paper_2406_10862_gb300 import partition as P
+    from paper_2406_10862_gb300 import workloads as W
+    g, s = W.layered_box()
+    slab = P.slab_of(g.nz, g.nx * g.ny, rank, world)
+    if slab.k1 <= slab.k0:
+        return 0, 0.0
+    h = P.subgrid(g, slab)
+    cells = slab.global_cells
+    t0 = time.perf_counter()
+    linearize(h, s.u_new[:, cells], s.flag_new[cells], s.u_old[:, cells], s.flag_old[cells], s.dt)
+    return (slab.k1 - slab.k0) * slab.nxy, time.perf_counter() - t0
+
+
+def oracle_all_cores():
+    """The oracle's linearisation of the whole 200 000-cell workload on every
+    host core: the box split into one slab per core (with ghost layers), one
+    spawned process per slab, timed from the start of the first to the end of
+    the last after the processes have started."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    world = min(cores, 20)                      # at least one layer per slab
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(world) as pool:
+        pool.map(_oracle_slab_task, [(0, 20)] * world)     # warm-up: start-up and imports
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_slab_task, [(r, world) for r in range(world)])
+        wall = time.perf_counter() - t0
+    owned = sum(n for n, _ in res)
+    return {"value": owned / wall / 1e6, "unit": "Mcell linearisations/s", "cores": world, "kind": "oracle",
+            "sample": "oracle linearisation (numpy) of the whole 100x100x20 workload split into %d slabs with "
+                      "ghost layers, one spawned process per slab; wall %.1f s" % (world, wall)}
+
+
+def host_info():
+    import platform
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"machine": platform.machine(), "cpus": os.cpu_count(), "model": model}
+
+
 def cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp):
     return t_lin + N_SPMV * t_spmv + t_vjp
 
@@ -382,6 +436,8 @@ def run_gpu(args, rank, world, local_rank):
             t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s)
             cpu = 1e-6 / cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp)
             line["cpu_baseline"] = {"value": cpu, "unit": "Mcell/s", "cores": 1, "kind": "oracle", "sample": desc}
+            line["cpu_baseline_all_cores"] = oracle_all_cores()
+            line["host"] = host_info()
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

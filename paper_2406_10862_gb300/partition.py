@@ -90,3 +90,40 @@ def exchange_ghosts(u: torch.Tensor, slab: Slab, group=None):
     if slab.hi:
         u[:, (slab.lo + nl) * nxy:] = hi_ghost
     return u
+
+
+def exchange_ghost_blocks(x: torch.Tensor, slab: Slab, nb: int, group=None):
+    """Fill the ghost layers of a block-interleaved sub-grid vector x
+    [n_sub * nb] (the layout of residuals and SpMV operands) in place."""
+    exchange_ghosts(x.view(-1, nb).t(), slab, group)
+    return x
+
+
+def distributed_spmv(apply, x: torch.Tensor, slab: Slab, nb: int, group=None):
+    """y = A x on a slab: the ghost layers of x are exchanged first, then
+    ``apply`` (the sub-grid's block-CSR product, e.g. ``Grid.spmv``) runs on
+    the whole sub-grid vector.  The owned rows of the result equal the same
+    rows of the product on the whole grid: each owned row reads only owned and
+    ghost cells, with the same blocks in the same order."""
+    exchange_ghost_blocks(x, slab, nb, group)
+    return apply(x)
+
+
+def owned_rows(v: torch.Tensor, slab: Slab, nb: int):
+    """The owned part of a block-interleaved sub-grid vector."""
+    return v.view(-1, nb)[slab.owned]
+
+
+def global_dot(a: torch.Tensor, b: torch.Tensor, group=None):
+    """Sum over all ranks of the dot product of their owned parts (the
+    Allreduce of the norms, Sec. 3.4.2)."""
+    t = (a * b).sum().reshape(1).to(torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t[0]
+
+
+def global_max(v: torch.Tensor, group=None):
+    """Largest entry over all ranks (for the scaled-residual maxima)."""
+    t = v.max().reshape(1).to(torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return t[0]

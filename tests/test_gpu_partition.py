@@ -39,3 +39,29 @@ def test_partitioned_linearization_is_bit_identical(world):
         v9 = v.reshape(-1, 9)
         for lc, gc in zip(range(own.start, own.stop), gown):
             assert np.array_equal(vs[rps[lc]:rps[lc + 1]], v9[rp[gc]:rp[gc + 1]])
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_partitioned_spmv_owned_rows_are_bit_identical(world):
+    # each sub-grid's product with a vector whose ghost layers hold the
+    # neighbours' entries reproduces the whole grid's owned rows bit for bit
+    need_gpu()
+    from paper_2406_10862_gb300 import ocp
+    from paper_2406_10862_gb300 import partition as P
+    g, s = W.layered_box(seed=10, nx=19, ny=13, nz=9, frac_unsat=0.2)
+    full = ocp.Grid(g)
+    _, v, _ = full.linearize(*dev_state(s), s.dt)
+    x = torch.as_tensor(np.random.default_rng(6).normal(size=3 * g.N), device="cuda")
+    y = full.spmv(v, x).cpu().numpy().reshape(-1, 3)
+    for rank in range(world):
+        slab = P.slab_of(g.nz, g.nx * g.ny, rank, world)
+        h = P.subgrid(g, slab)
+        cells = slab.global_cells
+        sub = W.State(u_new=s.u_new[:, cells], flag_new=s.flag_new[cells], u_old=s.u_old[:, cells],
+                      flag_old=s.flag_old[cells], dt=s.dt)
+        grid = ocp.Grid(h)
+        _, vs, _ = grid.linearize(*dev_state(sub), s.dt)
+        xs = x.view(-1, 3)[torch.as_tensor(cells, device="cuda")].reshape(-1).contiguous()
+        ys = grid.spmv(vs, xs)
+        got = P.owned_rows(ys, slab, 3).cpu().numpy()
+        assert np.array_equal(got, y[cells[slab.owned]])

@@ -84,3 +84,62 @@ def test_partitioned_rows_are_bit_identical(world):
         well_total += wsum
     assert seen.all()
     assert well_total == pytest.approx(float(full["well_rate"].sum()), rel=1e-13)
+
+
+def _spmv_worker(rank, world, port, out_q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle.linearize import linearize
+        from oracle.spmv import bsr_spmv
+        from paper_2406_10862_gb300 import partition as P
+        from paper_2406_10862_gb300 import workloads as W
+        g, s = W.tiny(4, 5, 8, seed=78, frac_unsat=0.3)
+        nb = g.nphase
+        slab = P.slab_of(g.nz, g.nx * g.ny, rank, world)
+        h = P.subgrid(g, slab)
+        cells = slab.global_cells
+        own = slab.owned
+        # the sub-grid's Jacobian from the exchanged state (as above)
+        o = linearize(h, s.u_new[:, cells], s.flag_new[cells], s.u_old[:, cells], s.flag_old[cells], s.dt)
+        x_glob = np.random.default_rng(5).normal(size=(g.N, nb))
+        x = torch.zeros((len(cells), nb), dtype=torch.float64)
+        x[own] = torch.from_numpy(x_glob[cells[own]])           # owned part only; ghosts arrive by exchange
+        apply = lambda v: torch.from_numpy(
+            bsr_spmv(o["row_ptr"], o["col_idx"], o["val"], v.numpy().ravel())[0].copy())
+        y = P.distributed_spmv(apply, x.view(-1), slab, nb)
+        y_own = P.owned_rows(y, slab, nb).numpy().copy()
+        d = P.global_dot(P.owned_rows(y, slab, nb), P.owned_rows(y, slab, nb))
+        m = P.global_max(P.owned_rows(y, slab, nb).abs())
+        out_q.put((rank, cells[own], y_own, float(d), float(m)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_distributed_spmv_rows_and_norms(world):
+    from oracle.linearize import linearize
+    from oracle.spmv import bsr_spmv
+    from paper_2406_10862_gb300 import workloads as W
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_spmv_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    g, s = W.tiny(4, 5, 8, seed=78, frac_unsat=0.3)
+    o = linearize(g, s.u_new, s.flag_new, s.u_old, s.flag_old, s.dt)
+    x = np.random.default_rng(5).normal(size=(g.N, g.nphase))
+    y = bsr_spmv(o["row_ptr"], o["col_idx"], o["val"], x.ravel())[0].reshape(-1, g.nphase)
+    seen = np.zeros(g.N, dtype=bool)
+    for rank, gown, y_own, d, m in res:
+        assert np.array_equal(y_own, y[gown])          # owned rows bit for bit
+        assert d == pytest.approx(float((y * y).sum()), rel=1e-13)
+        assert m == float(np.abs(y).max())
+        seen[gown] = True
+    assert seen.all()
