@@ -294,17 +294,42 @@ def run_gpu(args, rank, world, local_rank):
     flush = torch.empty(max(4 * l2, 512 * 2 ** 20) // 8, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(ev=None):
-        if ev is not None:
-            ev[0].record(stream)
+    def lin():
         grid.linearize(un, fn, uo, fo, s.dt, r, v, ff)
-        if ev is not None:
-            ev[1].record(stream)
+
+    def spmvs():
         for k in range(N_SPMV):
             grid.spmv(v, xs[k % 5], 1.0, 0.0, y)
-        if ev is not None:
-            ev[2].record(stream)
+
+    def vjp():
         grid.adjoint_vjp(un, fn, uo, fo, s.dt, v, ff, lam, out=gout)
+
+    phases = [lin, spmvs, vjp]
+    if not args.no_graph:
+        # each phase captured once as a CUDA graph and replayed: the same
+        # kernels on the same buffers, without the Python binding's per-call
+        # launch overhead between them
+        for f in phases:
+            f()
+        torch.cuda.synchronize(dev)
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        graphs = []
+        with torch.cuda.stream(side):
+            for f in phases:
+                gr = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gr, stream=side):
+                    f()
+                graphs.append(gr)
+        stream.wait_stream(side)
+        torch.cuda.synchronize(dev)
+        phases = [gr.replay for gr in graphs]
+
+    def step(ev=None):
+        for i, f in enumerate(phases):
+            if ev is not None:
+                ev[i].record(stream)
+            f()
         if ev is not None:
             ev[3].record(stream)
 
@@ -404,7 +429,9 @@ def run_gpu(args, rank, world, local_rank):
             "config": {"workload": "layered black-oil box 100x100x20 (200000 cells, 3x3 BSR, 1372000 blocks)",
                        "step": "linearize + 50 SpMV + adjoint VJP", "global_batch": world,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "flushed before every step (512 MB write outside the step events)"},
+                       "l2": "flushed before every step (512 MB write outside the step events)",
+                       "launch": "per-call launches" if args.no_graph else
+                                 "each phase (linearise, 50 SpMV, adjoint) replayed as a CUDA graph"},
             "phases_ms": {"linearize": statistics.mean(lin), "spmv_each": spmv_ms, "vjp": statistics.mean(vjp),
                           "wall_timed_region_ms": wall * 1e3},
             "roofline": {"kernel": "spmv_grid_kernel<3>", "bound": "alu", "achieved": achieved,
@@ -909,6 +936,8 @@ def main():
                     help="skip the 300-cell, oil-water and history-match measurements")
     ap.add_argument("--only", choices=["coupling", "wells", "pn", "impec", "small_case", "oil_water", "adjoint", "ensemble"],
                     help="only that side measurement, printed as one JSON line")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the step's kernels one call at a time instead of replaying per-phase CUDA graphs")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, no CPU baseline): the command profiled by ncu")
     args = ap.parse_args()
