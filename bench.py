@@ -41,6 +41,22 @@ def env_int(name, default):
         return default
 
 
+# DRAM bytes (read + write) of one spmv_grid_kernel<3> launch on the
+# 100x100x20 workload from the ncu capture summarised in
+# profiles/layered_box_kernels_full.md, valid for the kernel sources whose
+# hash is given; any change to them makes the figure void (reported null).
+SPMV_TRAFFIC = {"sources_sha256_16": "3e5bd05f6d88f629", "bytes": 107.83e6}
+
+
+def spmv_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("paper_2406_10862_gb300/csrc/spmv_adjoint.cu", "paper_2406_10862_gb300/csrc/ocp_internal.cuh"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return SPMV_TRAFFIC["bytes"] if h.hexdigest()[:16] == SPMV_TRAFFIC["sources_sha256_16"] else None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -438,7 +454,7 @@ def run_gpu(args, rank, world, local_rank):
                          "peak": fp64_peak, "unit": "GFLOP/s", "frac": achieved / fp64_peak,
                          "peak_source": "FP64 FMA rate measured in this run by ocp_probe_fp64 "
                                         "(nominal %.0f GFLOP/s)" % FP64_NOMINAL_GFLOPS,
-                         "traffic": None,
+                         "traffic": spmv_traffic(),
                          "hbm": {"algorithmic_bytes": hbm_bytes,
                                  "achieved_gbs": hbm_bytes / (spmv_ms * 1e-3) / 1e9,
                                  "peak_gbs": hbm_peak,
