@@ -11,6 +11,8 @@ the same sums; the plain relative error is meaningless where terms cancel.
 import numpy as np
 import pytest
 
+from paper_2406_10862_gb300 import workloads as W
+
 torch = pytest.importorskip("torch")
 
 RTOL_R = 1e-12
@@ -49,3 +51,33 @@ def assert_scaled_close(got, ref, mag, rtol, what):
         raise AssertionError("%s: %d of %d entries off; worst index %d got %.17g ref %.17g scale %.3g "
                              "(err/scale %.3g)" % (what, len(bad), len(err), k, got[k], ref[k], mag[k],
                                                     err[k] / max(mag[k], 1e-300)))
+
+
+def window(g, s, c, with_well_index=False):
+    """The 3x3x3 (clipped) window around cell c as a grid of its own: the
+    centre cell's residual row depends on nothing outside it.  With
+    ``with_well_index`` also the original index of every well kept."""
+    nx, ny, nz = g.nx, g.ny, g.nz
+    i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+    i0, i1, j0, j1, k0, k1 = max(i - 1, 0), min(i + 2, nx), max(j - 1, 0), min(j + 2, ny), max(k - 1, 0), min(k + 2, nz)
+    kk, jj, ii = np.meshgrid(np.arange(k0, k1), np.arange(j0, j1), np.arange(i0, i1), indexing="ij")
+    cells = (ii + nx * (jj + ny * kk)).ravel()
+    local = {int(x): n for n, x in enumerate(cells)}
+    wells = []
+    kept = []
+    for iw, w in enumerate(g.wells):
+        inside = [local[int(x)] for x in w.cells if int(x) in local]
+        if inside:
+            wells.append(W.Well(kind=w.kind, phase=w.phase, p_bh=w.p_bh, rw=w.rw, skin=w.skin,
+                                cells=np.array(inside, dtype=np.int64)))
+            kept.append(iw)
+    h = W.GridDesc(**{f: getattr(g, f) for f in g.__dataclass_fields__})
+    h.nx, h.ny, h.nz = i1 - i0, j1 - j0, k1 - k0
+    h.top_depth = g.top_depth + k0 * g.dz
+    h.lnk, h.phi, h.wells = g.lnk[cells], g.phi[cells], wells
+    st = W.State(u_new=s.u_new[:, cells], flag_new=s.flag_new[cells], u_old=s.u_old[:, cells],
+                 flag_old=s.flag_old[cells], dt=s.dt)
+    centre = local[int(c)]
+    if with_well_index:
+        return h, st, centre, cells, kept
+    return h, st, centre

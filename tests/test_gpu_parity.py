@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from _gpu_common import (RTOL_J, RTOL_R, RTOL_SPMV, RTOL_VJP, assert_scaled_close, dev_state,
-                         gpu_linearize, need_gpu, torch)
+                         gpu_linearize, need_gpu, torch, window)
 from oracle.linearize import linearize as oracle_linearize
 from oracle.spmv import bsr_spmv as oracle_spmv
 from paper_2406_10862_gb300 import workloads as W
@@ -213,31 +213,6 @@ def test_layered_box_full_size():
     ref, mag = oracle_spmv(o["row_ptr"], o["col_idx"], A, x, rows=rows)
     sel = (rows[:, None] * 3 + np.arange(3)).ravel()
     assert_scaled_close(y[sel], ref[sel], mag[sel], RTOL_SPMV, "spmv rows")
-
-
-def window(g, s, c):
-    """The 3x3x3 (clipped) window around cell c as a grid of its own: the
-    centre cell's residual row depends on nothing outside it."""
-    nx, ny, nz = g.nx, g.ny, g.nz
-    i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
-    i0, i1, j0, j1, k0, k1 = max(i - 1, 0), min(i + 2, nx), max(j - 1, 0), min(j + 2, ny), max(k - 1, 0), min(k + 2, nz)
-    kk, jj, ii = np.meshgrid(np.arange(k0, k1), np.arange(j0, j1), np.arange(i0, i1), indexing="ij")
-    cells = (ii + nx * (jj + ny * kk)).ravel()
-    local = {int(x): n for n, x in enumerate(cells)}
-    wells = []
-    for w in g.wells:
-        inside = [local[int(x)] for x in w.cells if int(x) in local]
-        if inside:
-            wells.append(W.Well(kind=w.kind, phase=w.phase, p_bh=w.p_bh, rw=w.rw, skin=w.skin,
-                                cells=np.array(inside, dtype=np.int64)))
-    h = W.GridDesc(**{f: getattr(g, f) for f in g.__dataclass_fields__})
-    h.nx, h.ny, h.nz = i1 - i0, j1 - j0, k1 - k0
-    h.top_depth = g.top_depth + k0 * g.dz
-    h.lnk, h.phi, h.wells = g.lnk[cells], g.phi[cells], wells
-    st = W.State(u_new=s.u_new[:, cells], flag_new=s.flag_new[cells], u_old=s.u_old[:, cells],
-                 flag_old=s.flag_old[cells], dt=s.dt)
-    centre = local[int(c)]
-    return h, st, centre
 
 
 def test_channelised_oil_water_full_size_sampled():
