@@ -58,6 +58,8 @@ void free_grid(ocp_grid* g) {
   cudaFree(g->d_status);
   cudaFree(g->d_scratch);
   cudaFree(g->d_pn);
+  if (g->solve_exec) cudaGraphExecDestroy(g->solve_exec);
+  if (g->solve_cap) cudaStreamDestroy(g->solve_cap);
   cudaFree(g->d_pn_flag);
   delete g;
 }

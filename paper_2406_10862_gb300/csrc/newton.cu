@@ -23,7 +23,12 @@ constexpr int kRedBlocks = 304;       // fixed partial-sum grid (2 per SM)
 constexpr int kRedThreads = 256;
 
 // scalar slots of the solver
-enum { S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_R0V, S_TS, S_TT, S_RR, S_BB, S_FLAG, S_TMP, S_COUNT };
+// S_DONE, S_ITER, S_TARGET, S_MAXIT drive the device-side iteration control
+enum {
+  S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_R0V, S_TS, S_TT, S_RR, S_BB, S_FLAG, S_TMP,
+  S_DONE, S_ITER, S_TARGET, S_MAXIT, S_COUNT
+};
+constexpr int kItersPerGraph = 8;     // BiCGSTAB iterations per graph replay
 
 __global__ void __launch_bounds__(kRedThreads) dot_partial(long long n, const double* __restrict__ a,
                                                             const double* __restrict__ b,
@@ -54,37 +59,59 @@ __global__ void __launch_bounds__(kRedThreads) dot_final(const double* __restric
   if (threadIdx.x == 0) *out = sh[0];
 }
 
+// Start of an iteration (one thread): the loop's test, on the device.  Once
+// the residual is small enough, a breakdown was flagged, the residual is not
+// finite or maxit iterations ran, S_DONE is set and every later update kernel
+// returns at once, so replaying more iterations than needed changes nothing.
+__global__ void iter_begin(double* sc) {
+  if (sc[S_DONE] != 0.0) return;
+  const double res = sqrt(sc[S_RR]);
+  if (sc[S_FLAG] != 0.0 || !(res > sc[S_TARGET]) || !(sc[S_ITER] < sc[S_MAXIT])) {
+    sc[S_DONE] = 1.0;
+    return;
+  }
+  sc[S_ITER] += 1.0;
+}
+
 // BiCGSTAB scalar steps (one thread).  S_FLAG records a breakdown.
 __global__ void scal_beta(double* sc) {
+  if (sc[S_DONE] != 0.0) return;
   const double rho = sc[S_RHO];
   if (sc[S_RHO_OLD] == 0.0 || sc[S_OMEGA] == 0.0) { sc[S_FLAG] = 1.0; sc[S_BETA] = 0.0; return; }
   sc[S_BETA] = (rho / sc[S_RHO_OLD]) * (sc[S_ALPHA] / sc[S_OMEGA]);
 }
 __global__ void scal_alpha(double* sc) {
+  if (sc[S_DONE] != 0.0) return;
   if (sc[S_R0V] == 0.0) { sc[S_FLAG] = 1.0; sc[S_ALPHA] = 0.0; return; }
   sc[S_ALPHA] = sc[S_RHO] / sc[S_R0V];
 }
 __global__ void scal_omega(double* sc) {
+  if (sc[S_DONE] != 0.0) return;
   if (sc[S_TT] == 0.0) { sc[S_OMEGA] = 0.0; return; }   // s == 0: x is already exact
   sc[S_OMEGA] = sc[S_TS] / sc[S_TT];
   sc[S_RHO_OLD] = sc[S_RHO];
 }
 __global__ void scal_init(double* sc) {
   sc[S_RHO_OLD] = 1.0; sc[S_ALPHA] = 1.0; sc[S_OMEGA] = 1.0; sc[S_FLAG] = 0.0; sc[S_BETA] = 0.0;
+  sc[S_DONE] = 0.0; sc[S_ITER] = 0.0;
+}
+__global__ void iter_setup(double* sc, double target, double maxit) {
+  sc[S_TARGET] = target;
+  sc[S_MAXIT] = maxit;
 }
 
 // p = r + beta (p - omega v)
 __global__ void upd_p(long long n, const double* __restrict__ r, double* __restrict__ p,
                       const double* __restrict__ v, const double* __restrict__ sc) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || sc[S_DONE] != 0.0) return;
   p[i] = fma(sc[S_BETA], fma(-sc[S_OMEGA], v[i], p[i]), r[i]);
 }
 // s = r - alpha v
 __global__ void upd_s(long long n, const double* __restrict__ r, const double* __restrict__ v,
                       double* __restrict__ s, const double* __restrict__ sc) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || sc[S_DONE] != 0.0) return;
   s[i] = fma(-sc[S_ALPHA], v[i], r[i]);
 }
 // x += alpha y + omega z;  r = s - omega t
@@ -92,7 +119,7 @@ __global__ void upd_xr(long long n, double* __restrict__ x, const double* __rest
                        const double* __restrict__ z, double* __restrict__ r, const double* __restrict__ s,
                        const double* __restrict__ t, const double* __restrict__ sc) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || sc[S_DONE] != 0.0) return;
   x[i] = fma(sc[S_OMEGA], z[i], fma(sc[S_ALPHA], y[i], x[i]));
   r[i] = fma(-sc[S_OMEGA], t[i], s[i]);
 }
@@ -307,12 +334,6 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
   else
     block_jacobi_kernel<1><<<bc, 256, 0, s>>>(g->prm, g->d_row_ptr, val, dinv, transpose, g->d_status,
                                               g->d_perf_of_cell, g->d_perf, wsv);
-  // the operator: A, or A - bs d^-1 cs with well terms
-  auto op = [&](const double* in, double* out) {
-    cudaError_t err = launch_spmv(g, val, 1.0, in, 0.0, out, transpose, s, nb);
-    if (err == cudaSuccess && ws) err = launch_well_schur(g, *ws, 0, -1.0, in, out, nullptr, nullptr, s);
-    return err;
-  };
   // Left block-Jacobi preconditioning: BiCGSTAB on D^-1 A x = D^-1 b, so the
   // residual that is tested is scaled cell by cell into the units of the
   // unknowns (psi, saturation, scf/stb) and no equation dominates its norm.
@@ -333,35 +354,81 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab: %s", cudaGetErrorString(e));
   const double bnorm = std::sqrt(h[S_BB]);
-  double res = std::sqrt(h[S_RR]);
-  int it = 0;
   const double target = rtol * (bnorm > 0.0 ? bnorm : 1.0);
-  while (res > target && it < maxit) {
-    ++it;
-    dot(r0, r, S_RHO);
-    scal_beta<<<1, 1, 0, s>>>(sc);
-    upd_p<<<bn, 256, 0, s>>>(n, r, p, v, sc);
+  // One iteration's kernels; the loop test runs on the device (iter_begin),
+  // so kItersPerGraph iterations are captured once into a CUDA graph, kept
+  // on the grid for the same buffers, and replayed until S_DONE.
+  auto iteration = [&](cudaStream_t cs) {
+    auto dot_s = [&](const double* a, const double* c, int slot) {
+      dot_partial<<<kRedBlocks, kRedThreads, 0, cs>>>(n, a, c, part);
+      dot_final<<<1, kRedThreads, 0, cs>>>(part, sc + slot);
+    };
+    auto apply_s = [&](const double* in, double* out) {
+      if (nb == 3) bj_apply_kernel<3><<<bc, 256, 0, cs>>>(N, dinv, in, out);
+      else if (nb == 2) bj_apply_kernel<2><<<bc, 256, 0, cs>>>(N, dinv, in, out);
+      else bj_apply_kernel<1><<<bc, 256, 0, cs>>>(N, dinv, in, out);
+    };
+    auto op_s = [&](const double* in, double* out) {
+      cudaError_t err = launch_spmv(g, val, 1.0, in, 0.0, out, transpose, cs, nb);
+      if (err == cudaSuccess && ws) err = launch_well_schur(g, *ws, 0, -1.0, in, out, nullptr, nullptr, cs);
+      return err;
+    };
+    cudaError_t err = cudaSuccess;
+    iter_begin<<<1, 1, 0, cs>>>(sc);
+    dot_s(r0, r, S_RHO);
+    scal_beta<<<1, 1, 0, cs>>>(sc);
+    upd_p<<<bn, 256, 0, cs>>>(n, r, p, v, sc);
     // v = D^-1 A p
-    e = op(p, z);
-    apply(z, v);
-    dot(r0, v, S_R0V);
-    scal_alpha<<<1, 1, 0, s>>>(sc);
-    upd_s<<<bn, 256, 0, s>>>(n, r, v, sv, sc);
+    if (err == cudaSuccess) err = op_s(p, z);
+    apply_s(z, v);
+    dot_s(r0, v, S_R0V);
+    scal_alpha<<<1, 1, 0, cs>>>(sc);
+    upd_s<<<bn, 256, 0, cs>>>(n, r, v, sv, sc);
     // t = D^-1 A s
-    if (e == cudaSuccess) e = op(sv, z);
-    apply(z, t);
-    dot(t, sv, S_TS);
-    dot(t, t, S_TT);
-    scal_omega<<<1, 1, 0, s>>>(sc);
+    if (err == cudaSuccess) err = op_s(sv, z);
+    apply_s(z, t);
+    dot_s(t, sv, S_TS);
+    dot_s(t, t, S_TT);
+    scal_omega<<<1, 1, 0, cs>>>(sc);
     // x += alpha p + omega s;  r = s - omega t
-    upd_xr<<<bn, 256, 0, s>>>(n, x, p, sv, r, sv, t, sc);
-    dot(r, r, S_RR);
+    upd_xr<<<bn, 256, 0, cs>>>(n, x, p, sv, r, sv, t, sc);
+    dot_s(r, r, S_RR);
+    return err;
+  };
+  const void* key[8] = {val, work, x, ws ? ws->bs : nullptr, ws ? ws->cs : nullptr, ws ? ws->d : nullptr,
+                        (const void*)(intptr_t)(transpose ? 1 : 0), (const void*)(intptr_t)nb};
+  bool same = g->solve_exec != nullptr;
+  for (int k = 0; k < 8 && same; ++k) same = g->solve_key[k] == key[k];
+  if (!same) {
+    if (g->solve_exec) {
+      cudaGraphExecDestroy(g->solve_exec);
+      g->solve_exec = nullptr;
+    }
+    if (!g->solve_cap) e = cudaStreamCreateWithFlags(&g->solve_cap, cudaStreamNonBlocking);
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(g->solve_cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t er = cudaSuccess;
+      for (int k = 0; k < kItersPerGraph && er == cudaSuccess; ++k) er = iteration(g->solve_cap);
+      e = cudaStreamEndCapture(g->solve_cap, &graph);
+      if (e == cudaSuccess) e = er;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->solve_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab capture: %s", cudaGetErrorString(e));
+    for (int k = 0; k < 8; ++k) g->solve_key[k] = key[k];
+  }
+  iter_setup<<<1, 1, 0, s>>>(sc, target, (double)maxit);
+  const int max_replays = maxit / kItersPerGraph + 2;
+  for (int rep = 0; rep < max_replays; ++rep) {
+    e = cudaGraphLaunch(g->solve_exec, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab: %s", cudaGetErrorString(e));
-    res = std::sqrt(h[S_RR]);
-    if (h[S_FLAG] != 0.0 || !std::isfinite(res)) break;
+    if (h[S_DONE] != 0.0) break;
   }
+  const int it = (int)h[S_ITER];
+  const double res = std::sqrt(h[S_RR]);
   if (iters) *iters = it;
   if (relres) *relres = bnorm > 0.0 ? res / bnorm : res;
   if (!std::isfinite(res)) return report(OCP_ERR_NONFINITE, "ocp_bicgstab: non-finite residual");

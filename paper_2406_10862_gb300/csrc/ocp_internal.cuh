@@ -104,6 +104,9 @@ struct ocp_grid {
   double* d_scratch;         // per-cell scratch of the linearisation
   double* d_pn;              // per-cell data of the (P, N) path, allocated on its first use
   int8_t* d_pn_flag;
+  cudaStream_t solve_cap;    // private stream on which the solver's iterations are captured
+  cudaGraphExec_t solve_exec;  // a block of solver iterations, valid for the buffers in solve_key
+  const void* solve_key[8];
   int64_t scratch_doubles;
   ocp::LaunchCfg cfg;        // launch shape of the linearisation
   int sms;                   // SM count of the device
