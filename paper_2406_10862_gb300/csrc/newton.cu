@@ -59,38 +59,155 @@ __global__ void __launch_bounds__(kRedThreads) dot_final(const double* __restric
   if (threadIdx.x == 0) *out = sh[0];
 }
 
-// Start of an iteration (one thread): the loop's test, on the device.  Once
-// the residual is small enough, a breakdown was flagged, the residual is not
-// finite or maxit iterations ran, S_DONE is set and every later update kernel
-// returns at once, so replaying more iterations than needed changes nothing.
-__global__ void iter_begin(double* sc) {
-  if (sc[S_DONE] != 0.0) return;
-  const double res = sqrt(sc[S_RR]);
-  if (sc[S_FLAG] != 0.0 || !(res > sc[S_TARGET]) || !(sc[S_ITER] < sc[S_MAXIT])) {
-    sc[S_DONE] = 1.0;
-    return;
+// ------------------------------------------------------------ fused steps
+// The kernels below fuse a vector step with the dot products that follow it.
+// They use the same fixed grid and the same element-to-thread assignment,
+// per-thread order and tree as dot_partial / dot_final, so every sum is the
+// bit-identical value the separate kernels gave.
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&v)[NV], double* __restrict__ part) {
+  __shared__ double sh[NV][kRedThreads];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
   }
-  sc[S_ITER] += 1.0;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) part[q * kRedBlocks + blockIdx.x] = sh[q][0];
 }
 
-// BiCGSTAB scalar steps (one thread).  S_FLAG records a breakdown.
-__global__ void scal_beta(double* sc) {
-  if (sc[S_DONE] != 0.0) return;
-  const double rho = sc[S_RHO];
-  if (sc[S_RHO_OLD] == 0.0 || sc[S_OMEGA] == 0.0) { sc[S_FLAG] = 1.0; sc[S_BETA] = 0.0; return; }
-  sc[S_BETA] = (rho / sc[S_RHO_OLD]) * (sc[S_ALPHA] / sc[S_OMEGA]);
+__device__ __forceinline__ double block_total(const double* __restrict__ part) {
+  __shared__ double sh[kRedThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double t = sh[0];
+  __syncthreads();
+  return t;
 }
-__global__ void scal_alpha(double* sc) {
-  if (sc[S_DONE] != 0.0) return;
-  if (sc[S_R0V] == 0.0) { sc[S_FLAG] = 1.0; sc[S_ALPHA] = 0.0; return; }
-  sc[S_ALPHA] = sc[S_RHO] / sc[S_R0V];
+
+// element i of the block-Jacobi product D^-1 z (the order of bj_apply_kernel)
+template <int NB>
+__device__ __forceinline__ double bj_elem(const double* __restrict__ dinv, const double* __restrict__ z, long long i) {
+  const long long c = i / NB;
+  const int e = (int)(i - c * NB);
+  double s = 0.0;
+#pragma unroll
+  for (int v = 0; v < NB; ++v) s = fma(dinv[c * NB * NB + e * NB + v], z[c * NB + v], s);
+  return s;
 }
-__global__ void scal_omega(double* sc) {
+
+// v = D^-1 z and the partials of r0 . v
+template <int NB>
+__global__ void __launch_bounds__(kRedThreads) apply_dot(long long n, const double* __restrict__ dinv,
+                                                          const double* __restrict__ z, double* __restrict__ v,
+                                                          const double* __restrict__ r0, const double* __restrict__ sc,
+                                                          double* __restrict__ part) {
   if (sc[S_DONE] != 0.0) return;
-  if (sc[S_TT] == 0.0) { sc[S_OMEGA] = 0.0; return; }   // s == 0: x is already exact
-  sc[S_OMEGA] = sc[S_TS] / sc[S_TT];
-  sc[S_RHO_OLD] = sc[S_RHO];
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
+    const double x = bj_elem<NB>(dinv, z, i);
+    v[i] = x;
+    acc[0] = fma(r0[i], x, acc[0]);
+  }
+  block_partials<1>(acc, part);
 }
+
+// t = D^-1 z and the partials of t . s and t . t
+template <int NB>
+__global__ void __launch_bounds__(kRedThreads) apply_dot2(long long n, const double* __restrict__ dinv,
+                                                           const double* __restrict__ z, double* __restrict__ t,
+                                                           const double* __restrict__ sv, const double* __restrict__ sc,
+                                                           double* __restrict__ part) {
+  if (sc[S_DONE] != 0.0) return;
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
+    const double x = bj_elem<NB>(dinv, z, i);
+    t[i] = x;
+    acc[0] = fma(x, sv[i], acc[0]);
+    acc[1] = fma(x, x, acc[1]);
+  }
+  block_partials<2>(acc, part);
+}
+
+// x += alpha p + omega s, r = s - omega t, and the partials of r . r and r0 . r
+__global__ void __launch_bounds__(kRedThreads) upd_xr_dot(long long n, double* __restrict__ x,
+                                                           const double* __restrict__ p, const double* __restrict__ sv,
+                                                           double* __restrict__ r, const double* __restrict__ t,
+                                                           const double* __restrict__ r0, const double* __restrict__ sc,
+                                                           double* __restrict__ part) {
+  if (sc[S_DONE] != 0.0) return;
+  const double al = sc[S_ALPHA], om = sc[S_OMEGA];
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
+    x[i] = fma(om, sv[i], fma(al, p[i], x[i]));
+    const double ri = fma(-om, t[i], sv[i]);
+    r[i] = ri;
+    acc[0] = fma(ri, ri, acc[0]);
+    acc[1] = fma(r0[i], ri, acc[1]);
+  }
+  block_partials<2>(acc, part);
+}
+
+// the partials of a1 . b1 and a2 . b2 (start of the iteration)
+__global__ void __launch_bounds__(kRedThreads) dot2_partial(long long n, const double* __restrict__ a1,
+                                                             const double* __restrict__ b1,
+                                                             const double* __restrict__ a2,
+                                                             const double* __restrict__ b2, double* __restrict__ part) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
+    acc[0] = fma(a1[i], b1[i], acc[0]);
+    acc[1] = fma(a2[i], b2[i], acc[1]);
+  }
+  block_partials<2>(acc, part);
+}
+
+// Totals and the scalar step after them (one CTA; thread 0 writes):
+//   kFinAlpha: r0.v -> alpha;  kFinOmega: t.s, t.t -> omega;
+//   kFinRrRho: r.r -> the loop's test for the next iteration (S_DONE or
+//   S_ITER + 1), then r0.r -> rho and beta.
+enum { kFinAlpha = 0, kFinOmega = 1, kFinRrRho = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads) fin_kernel(const double* __restrict__ part, double* __restrict__ sc) {
+  if (sc[S_DONE] != 0.0) return;
+  const double a = block_total(part);
+  const double b = (MODE == kFinAlpha) ? 0.0 : block_total(part + kRedBlocks);
+  if (threadIdx.x != 0) return;
+  if constexpr (MODE == kFinAlpha) {
+    sc[S_R0V] = a;
+    if (a == 0.0) { sc[S_FLAG] = 1.0; sc[S_ALPHA] = 0.0; return; }
+    sc[S_ALPHA] = sc[S_RHO] / a;
+  } else if constexpr (MODE == kFinOmega) {
+    sc[S_TS] = a;
+    sc[S_TT] = b;
+    if (b == 0.0) { sc[S_OMEGA] = 0.0; return; }   // s == 0: x is already exact
+    sc[S_OMEGA] = a / b;
+    sc[S_RHO_OLD] = sc[S_RHO];
+  } else {
+    sc[S_RR] = a;
+    const double res = sqrt(a);
+    if (sc[S_FLAG] != 0.0 || !(res > sc[S_TARGET]) || !(sc[S_ITER] < sc[S_MAXIT])) {
+      sc[S_DONE] = 1.0;
+      return;
+    }
+    sc[S_ITER] += 1.0;
+    sc[S_RHO] = b;
+    if (sc[S_RHO_OLD] == 0.0 || sc[S_OMEGA] == 0.0) { sc[S_FLAG] = 1.0; sc[S_BETA] = 0.0; return; }
+    sc[S_BETA] = (b / sc[S_RHO_OLD]) * (sc[S_ALPHA] / sc[S_OMEGA]);
+  }
+}
+
 __global__ void scal_init(double* sc) {
   sc[S_RHO_OLD] = 1.0; sc[S_ALPHA] = 1.0; sc[S_OMEGA] = 1.0; sc[S_FLAG] = 0.0; sc[S_BETA] = 0.0;
   sc[S_DONE] = 0.0; sc[S_ITER] = 0.0;
@@ -114,16 +231,6 @@ __global__ void upd_s(long long n, const double* __restrict__ r, const double* _
   if (i >= n || sc[S_DONE] != 0.0) return;
   s[i] = fma(-sc[S_ALPHA], v[i], r[i]);
 }
-// x += alpha y + omega z;  r = s - omega t
-__global__ void upd_xr(long long n, double* __restrict__ x, const double* __restrict__ y,
-                       const double* __restrict__ z, double* __restrict__ r, const double* __restrict__ s,
-                       const double* __restrict__ t, const double* __restrict__ sc) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n || sc[S_DONE] != 0.0) return;
-  x[i] = fma(sc[S_OMEGA], z[i], fma(sc[S_ALPHA], y[i], x[i]));
-  r[i] = fma(-sc[S_OMEGA], t[i], s[i]);
-}
-
 // Inverse of every diagonal block (of its transpose when TRANS).
 // With well terms, a perforated cell's block is that of the Schur complement,
 // A_cc - bs_c cs_c^T / d_w.
@@ -291,9 +398,9 @@ cudaError_t launch_perf_wi(ocp_grid* g, const double* lnk, cudaStream_t s) {
 
 int64_t solver_work_doubles(const ocp_grid* g) {
   const int64_t n = (int64_t)g->prm.nb * g->prm.N;
-  // r, r0, p, v, s, t, y, z; block inverses; partial sums; scalars; and the
-  // reduced right-hand side of the well elimination
-  return 9 * n + (int64_t)g->prm.nb * g->prm.nb * g->prm.N + kRedBlocks + S_COUNT + 8;
+  // r, r0, p, v, s, t, y, z; block inverses; two sets of partial sums;
+  // scalars; and the reduced right-hand side of the well elimination
+  return 9 * n + (int64_t)g->prm.nb * g->prm.nb * g->prm.N + 2 * kRedBlocks + S_COUNT + 8;
 }
 
 ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, const double* b, double* x,
@@ -311,8 +418,8 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
   double* y = t + n;
   double* z = y + n;
   double* dinv = z + n;
-  double* part = dinv + (long long)nb * nb * N;
-  double* sc = part + kRedBlocks;
+  double* part = dinv + (long long)nb * nb * N;     // 2 * kRedBlocks partial sums
+  double* sc = part + 2 * kRedBlocks;
   const unsigned bn = nblk(n), bc = nblk(N);
   auto dot = [&](const double* a, const double* c, int slot) {
     dot_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, a, c, part);
@@ -355,44 +462,35 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
   if (e != cudaSuccess) return report(OCP_ERR_CUDA, "ocp_bicgstab: %s", cudaGetErrorString(e));
   const double bnorm = std::sqrt(h[S_BB]);
   const double target = rtol * (bnorm > 0.0 ? bnorm : 1.0);
-  // One iteration's kernels; the loop test runs on the device (iter_begin),
-  // so kItersPerGraph iterations are captured once into a CUDA graph, kept
-  // on the grid for the same buffers, and replayed until S_DONE.
+  // One iteration's kernels; the loop's test runs on the device (at the end
+  // of the previous iteration, fin_kernel<kFinRrRho>), so kItersPerGraph
+  // iterations are captured once into a CUDA graph, kept on the grid for the
+  // same buffers, and replayed until S_DONE.
   auto iteration = [&](cudaStream_t cs) {
-    auto dot_s = [&](const double* a, const double* c, int slot) {
-      dot_partial<<<kRedBlocks, kRedThreads, 0, cs>>>(n, a, c, part);
-      dot_final<<<1, kRedThreads, 0, cs>>>(part, sc + slot);
-    };
-    auto apply_s = [&](const double* in, double* out) {
-      if (nb == 3) bj_apply_kernel<3><<<bc, 256, 0, cs>>>(N, dinv, in, out);
-      else if (nb == 2) bj_apply_kernel<2><<<bc, 256, 0, cs>>>(N, dinv, in, out);
-      else bj_apply_kernel<1><<<bc, 256, 0, cs>>>(N, dinv, in, out);
-    };
     auto op_s = [&](const double* in, double* out) {
       cudaError_t err = launch_spmv(g, val, 1.0, in, 0.0, out, transpose, cs, nb);
       if (err == cudaSuccess && ws) err = launch_well_schur(g, *ws, 0, -1.0, in, out, nullptr, nullptr, cs);
       return err;
     };
     cudaError_t err = cudaSuccess;
-    iter_begin<<<1, 1, 0, cs>>>(sc);
-    dot_s(r0, r, S_RHO);
-    scal_beta<<<1, 1, 0, cs>>>(sc);
+    // p = r + beta (p - omega v)   (beta from the end of the previous iteration)
     upd_p<<<bn, 256, 0, cs>>>(n, r, p, v, sc);
-    // v = D^-1 A p
+    // v = D^-1 A p, then alpha = rho / (r0 . v)
     if (err == cudaSuccess) err = op_s(p, z);
-    apply_s(z, v);
-    dot_s(r0, v, S_R0V);
-    scal_alpha<<<1, 1, 0, cs>>>(sc);
+    if (nb == 3) apply_dot<3><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, v, r0, sc, part);
+    else if (nb == 2) apply_dot<2><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, v, r0, sc, part);
+    else apply_dot<1><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, v, r0, sc, part);
+    fin_kernel<kFinAlpha><<<1, kRedThreads, 0, cs>>>(part, sc);
     upd_s<<<bn, 256, 0, cs>>>(n, r, v, sv, sc);
-    // t = D^-1 A s
+    // t = D^-1 A s, then omega = (t . s) / (t . t)
     if (err == cudaSuccess) err = op_s(sv, z);
-    apply_s(z, t);
-    dot_s(t, sv, S_TS);
-    dot_s(t, t, S_TT);
-    scal_omega<<<1, 1, 0, cs>>>(sc);
-    // x += alpha p + omega s;  r = s - omega t
-    upd_xr<<<bn, 256, 0, cs>>>(n, x, p, sv, r, sv, t, sc);
-    dot_s(r, r, S_RR);
+    if (nb == 3) apply_dot2<3><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, t, sv, sc, part);
+    else if (nb == 2) apply_dot2<2><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, t, sv, sc, part);
+    else apply_dot2<1><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, t, sv, sc, part);
+    fin_kernel<kFinOmega><<<1, kRedThreads, 0, cs>>>(part, sc);
+    // x += alpha p + omega s;  r = s - omega t;  then the loop's test, rho and beta
+    upd_xr_dot<<<kRedBlocks, kRedThreads, 0, cs>>>(n, x, p, sv, r, t, r0, sc, part);
+    fin_kernel<kFinRrRho><<<1, kRedThreads, 0, cs>>>(part, sc);
     return err;
   };
   const void* key[8] = {val, work, x, ws ? ws->bs : nullptr, ws ? ws->cs : nullptr, ws ? ws->d : nullptr,
@@ -419,6 +517,9 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
     for (int k = 0; k < 8; ++k) g->solve_key[k] = key[k];
   }
   iter_setup<<<1, 1, 0, s>>>(sc, target, (double)maxit);
+  // the loop's first test and the first rho and beta
+  dot2_partial<<<kRedBlocks, kRedThreads, 0, s>>>(n, r, r, r0, r, part);
+  fin_kernel<kFinRrRho><<<1, kRedThreads, 0, s>>>(part, sc);
   const int max_replays = maxit / kItersPerGraph + 2;
   for (int rep = 0; rep < max_replays; ++rep) {
     e = cudaGraphLaunch(g->solve_exec, s);
