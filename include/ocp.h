@@ -258,9 +258,13 @@ int64_t ocp_solver_work_doubles(const ocp_grid* grid);
  * scaled cell by cell into the units of the unknowns.  x holds the initial guess
  * on entry and the solution on return; b and x are block-interleaved [nb*N]
  * device vectors; work is a device buffer of ocp_solver_work_doubles().
- * Synchronises the stream once per iteration (to test convergence).  The
- * paper solves with CPR-preconditioned FGMRES in PETSc/Hypre (Sec. 5.1); this
- * plain Krylov solver serves the adjoint and test drivers.  Returns
+ * The iterations run as replays of a CUDA graph of eight iterations with the
+ * convergence test on the device; the stream is synchronised once per replay.
+ * The graph is captured on the first call and kept on the grid while the
+ * same bsr_val, x, work (and well terms) are passed; calls on one grid must
+ * not overlap from several host threads.  The paper solves with
+ * CPR-preconditioned FGMRES in PETSc/Hypre (Sec. 5.1); this plain Krylov
+ * solver serves the Newton, adjoint and test drivers.  Returns
  * OCP_ERR_TIMEOUT when maxit is reached, OCP_ERR_NONFINITE on breakdown;
  * *iters and *relres (may be NULL) report the final state. */
 ocp_status ocp_bicgstab(ocp_grid* grid, const double* bsr_val, const double* b, double* x, double rtol,
