@@ -37,8 +37,10 @@
  *   launched.  Errors found on the device (non-finite values, bad flags) are
  *   sticky in the grid's status word and reported by ocp_get_status().
  * There is no CPU fallback: every compute call runs CUDA kernels for sm_103a.
- * Only ocp_grid_create, ocp_batch_create and their destroy calls allocate or
- *   free device memory.
+ * Only ocp_grid_create, ocp_batch_create, their destroy calls and the first
+ *   ocp_linearize_pn on a grid (its phase-split data) allocate or free device
+ *   memory; the first ocp_bicgstab* call on a grid creates a stream and a
+ *   CUDA graph that the grid keeps.
  * ocp_last_error() returns a thread-local message describing the last failure.
  */
 #ifndef OCP_H
