@@ -904,6 +904,11 @@ def run_adjoint(dev, local_rank):
     _, _, rates = hm.run(T(lnk_truth))
     hm.q_obs = torch.stack(rates)
     hm.q_scale = hm.q_obs.abs().amax(dim=(0, 1)) + 1e-30
+    # one untimed forward and backward: the first use of torch's own
+    # elementwise kernels in the loss and the cotangent bookkeeping can
+    # include their just-in-time compilation
+    warm = T(lnk_prior).requires_grad_(True)
+    fim.HistoryMatchLoss.apply(warm, hm).backward()
     lnk = T(lnk_prior).requires_grad_(True)
     hm.stepper.newton_iters = hm.stepper.linear_iters = 0
     torch.cuda.synchronize(dev)
