@@ -465,9 +465,11 @@ def run_gpu(args, rank, world, local_rank):
             "clocks": clk.summary(),
             "device_status": st,
         }
-        if not args.no_ensemble:
+        # the side measurements are single-GPU figures: taken at N = 1 only, so
+        # that a multi-GPU run does not hold the other GPUs idle meanwhile
+        if not args.no_ensemble and world == 1:
             line["ensemble"] = run_ensemble(dev, local_rank, reps=max(5, min(args.steps, 20)))
-        if not args.no_extra:
+        if not args.no_extra and world == 1:
             line["small_case"] = run_small_case(dev, local_rank)
             line["oil_water"] = run_oil_water(dev, local_rank)
             line["adjoint"] = run_adjoint(dev, local_rank)
