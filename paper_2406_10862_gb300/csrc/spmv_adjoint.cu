@@ -237,28 +237,33 @@ __global__ void __launch_bounds__(256) vjp_kernel(Params P, const Table* __restr
   const int fn = (NB == 3) ? (f_new[c] & 1) : 0, fo = (NB == 3) ? (f_old[c] & 1) : 0;
   const double ph = phi[c];
 
-  if (g_uold) {
-    double m[3], m_p[3], m_sw[3], m_x[3];
-    cell_masses<NB, true>(P, T, po, swo, xo, fo, ph, m, m_p, m_sw, m_x);
-    double g[3] = {0.0, 0.0, 0.0};
+  if (g_uold || g_phi) {
+    // the accumulation is linear in the reference porosity: the amounts of
+    // the old state per unit phi_ref serve both outputs
+    double mo[3], m_p[3], m_sw[3], m_x[3];
+    cell_masses<NB, true>(P, T, po, swo, xo, fo, 1.0, mo, m_p, m_sw, m_x);
+    if (g_uold) {
+      double lph[NB];
 #pragma unroll
-    for (int e = 0; e < NB; ++e) {
-      g[0] = fma(lc[e], m_p[e], g[0]);
-      g[1] = fma(lc[e], m_sw[e], g[1]);
-      g[2] = fma(lc[e], m_x[e], g[2]);
+      for (int e = 0; e < NB; ++e) lph[e] = lc[e] * ph;
+      double g[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int e = 0; e < NB; ++e) {
+        g[0] = fma(lph[e], m_p[e], g[0]);
+        g[1] = fma(lph[e], m_sw[e], g[1]);
+        g[2] = fma(lph[e], m_x[e], g[2]);
+      }
+#pragma unroll
+      for (int v = 0; v < NB; ++v) g_uold[v * N + c] = -scale * g[v];
     }
+    if (g_phi) {
+      double mn[3];
+      cell_masses<NB, false>(P, T, pn, swn, xn, fn, 1.0, mn);
+      double g = 0.0;
 #pragma unroll
-    for (int v = 0; v < NB; ++v) g_uold[v * N + c] = -scale * g[v];
-  }
-  if (g_phi) {
-    // the accumulation is linear in the reference porosity
-    double mn[3], mo[3];
-    cell_masses<NB, false>(P, T, pn, swn, xn, fn, 1.0, mn);
-    cell_masses<NB, false>(P, T, po, swo, xo, fo, 1.0, mo);
-    double g = 0.0;
-#pragma unroll
-    for (int e = 0; e < NB; ++e) g = fma(lc[e], mn[e] - mo[e], g);
-    g_phi[c] = scale * g;
+      for (int e = 0; e < NB; ++e) g = fma(lc[e], mn[e] - mo[e], g);
+      g_phi[c] = scale * g;
+    }
   }
 
   if (g_lnk) {
