@@ -172,13 +172,20 @@ def _check(st):
 
 
 def _ptr(t):
-    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    return t.data_ptr() if t is not None else None
+
+
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
 
 
 def _stream(device, stream):
+    """The CUDA stream handle for a call: the given torch stream, else the
+    device's current one (read without building a Stream object)."""
     if stream is None:
+        if _raw_stream is not None:
+            return _raw_stream(device.index if device.index is not None else torch.cuda.current_device())
         stream = torch.cuda.current_stream(device)
-    return ctypes.c_void_p(stream.cuda_stream)
+    return stream.cuda_stream
 
 
 class _DevView:
