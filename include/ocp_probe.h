@@ -15,9 +15,12 @@
 extern "C" {
 #endif
 
-/* Runs an FP64 FMA throughput kernel on `device` (16 independent FMA chains
- * per thread, 8 CTAs of 256 threads per SM) `reps` times and returns the best
- * rate in *dfma_per_s (FMA thread-operations per second; 2 flops each).
+/* Runs two FP64 FMA throughput kernels on `device` (16 independent FMA
+ * chains per thread, 8 CTAs of 256 threads per SM), `reps` times each: chains
+ * through the multiplicand with constant operands (v = v*a + b) and
+ * accumulation chains with loop-invariant register multiplicands
+ * (v = x*y + v), which GB300 issues about 18 % faster.  Returns the best rate
+ * of either in *dfma_per_s (FMA thread-operations per second; 2 flops each).
  * Allocates and frees a small device buffer; synchronises the device.
  * Returns OCP_ERR_INVALID_ARG for a NULL output or reps < 1. */
 ocp_status ocp_probe_fp64(int device, int reps, double* dfma_per_s);
