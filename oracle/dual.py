@@ -24,10 +24,21 @@ of the terms that were cancelled rather than against the tiny result.
 
 Branches (clamps, upwind choice) are decided on ``v`` only; the magnitude
 follows the branch that the value takes.
+
+Values may be complex: a complex input keeps ``v`` and ``g`` complex, so the
+same code evaluated at u + i h e_j yields the complex-step derivative
+Im R / h, which the tests use to pin the dual-number Jacobian.  Branches then
+compare complex values lexicographically (real part first), which away from
+exact ties is the comparison of the real parts.  Real inputs are unaffected.
 """
 from __future__ import annotations
 
 import numpy as np
+
+
+def _arr(x):
+    """float64 array, or complex128 where the input is complex."""
+    return np.asarray(x, dtype=np.complex128 if np.iscomplexobj(x) else np.float64)
 
 
 class D:
@@ -35,22 +46,22 @@ class D:
     __array_ufunc__ = None   # numpy scalars and arrays defer to D's operators
 
     def __init__(self, v, g, m=None, gm=None):
-        self.v = np.asarray(v, dtype=np.float64)
-        self.g = np.asarray(g, dtype=np.float64)
+        self.v = _arr(v)
+        self.g = _arr(g)
         self.m = np.abs(self.v) if m is None else np.asarray(m, dtype=np.float64)
         self.gm = np.abs(self.g) if gm is None else np.asarray(gm, dtype=np.float64)
 
     # ----------------------------------------------------------------- builders
     @staticmethod
     def const(c, n, k):
-        c = np.broadcast_to(np.asarray(c, dtype=np.float64), (n,)).copy()
+        c = np.broadcast_to(_arr(c), (n,)).copy()
         z = np.zeros((n, k))
         return D(c, z, np.abs(c), z.copy())
 
     @staticmethod
     def seed(v, k, j):
         """Independent variable number ``j`` of ``k``."""
-        v = np.asarray(v, dtype=np.float64)
+        v = _arr(v)
         g = np.zeros((v.shape[0], k))
         g[:, j] = 1.0
         return D(v, g, np.abs(v), g.copy())
@@ -71,7 +82,7 @@ class D:
     def embed(self, k, offset):
         """Same number seen as a function of ``k`` variables: the current
         derivative block moves to columns ``offset .. offset+self.k``."""
-        g = np.zeros((self.n, k))
+        g = np.zeros((self.n, k), dtype=self.g.dtype)
         gm = np.zeros((self.n, k))
         g[:, offset:offset + self.k] = self.g
         gm[:, offset:offset + self.k] = self.gm

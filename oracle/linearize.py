@@ -77,7 +77,8 @@ def transmissibility(spec, d, lnk_i: D, lnk_j: D) -> D:
 
 def _exp(a: D) -> D:
     e = np.exp(a.v)
-    return D(e, e[:, None] * a.g, np.exp(a.v), e[:, None] * a.gm)
+    ae = np.abs(e)                       # the magnitude (e itself for real a)
+    return D(e, e[:, None] * a.g, ae, ae[:, None] * a.gm)
 
 
 def well_index(spec, well, lnk_c: D) -> D:
@@ -137,10 +138,13 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
     N = nx * ny * nz
     nv = nb = int(spec.nphase)
     L = nv if mode == "unew" else 2 * nv + 2
-    u_new = np.asarray(u_new, dtype=np.float64).reshape(nv, N)
-    u_old = np.asarray(u_old, dtype=np.float64).reshape(nv, N)
-    lnk_v = np.asarray(spec.lnk, dtype=np.float64)
-    phi_v = np.asarray(spec.phi, dtype=np.float64)
+    # complex states give complex results (complex-step checks); real ones float64
+    cdt = np.result_type(np.asarray(u_new), np.asarray(u_old), np.asarray(spec.lnk), np.asarray(spec.phi),
+                         np.float64)
+    u_new = np.asarray(u_new, dtype=cdt).reshape(nv, N)
+    u_old = np.asarray(u_old, dtype=cdt).reshape(nv, N)
+    lnk_v = np.asarray(spec.lnk, dtype=cdt)
+    phi_v = np.asarray(spec.phi, dtype=cdt)
 
     un = [D.seed(u_new[v], L, v) for v in range(nv)]
     if mode == "all":
@@ -162,12 +166,12 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
     mn, mo = masses(spec, pn), masses(spec, po)
     acc = [(mn[e] - mo[e]) * (vol / RB_FT3) / dt for e in range(nb)]
 
-    R = np.zeros((N, nb))
+    R = np.zeros((N, nb), dtype=cdt)
     Rm = np.zeros((N, nb))
     row_ptr, col_idx, slot = bsr_pattern(spec)
-    val = np.zeros((len(col_idx), nb, nb))
+    val = np.zeros((len(col_idx), nb, nb), dtype=cdt)
     valm = np.zeros((len(col_idx), nb, nb))
-    gw = np.zeros((N, L)) if lam is not None else None
+    gw = np.zeros((N, L), dtype=cdt) if lam is not None else None
     gwm = np.zeros((N, L)) if lam is not None else None
     alam = np.abs(lam) if lam is not None else None
     cells = np.arange(N)
@@ -191,7 +195,7 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
     # ---- connection fluxes (BulkConn): two-point, phase-upwinded
     z = depth(spec)
     phases = ["w", "o", "g"][:nb]
-    face_flux = np.zeros((3, nb, N))
+    face_flux = np.zeros((3, nb, N), dtype=cdt)
     face_flux_mag = np.zeros((3, nb, N))
     face_dphi = {}
     for d in range(3):
@@ -250,13 +254,13 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
         p_bh = np.asarray(p_bh, dtype=np.float64)
         if controls is None:
             controls = [(0, 0, float(w.p_bh)) for w in spec.wells]
-        w_res = np.zeros(nwell)
+        w_res = np.zeros(nwell, dtype=cdt)
         w_res_m = np.zeros(nwell)
-        w_D = np.zeros(nwell)
+        w_D = np.zeros(nwell, dtype=cdt)
         w_D_m = np.zeros(nwell)
         w_B, w_B_m, w_C, w_C_m = [], [], [], []
-    well_q = np.zeros((N, nb))
-    well_rate = np.zeros((nwell, nb))
+    well_q = np.zeros((N, nb), dtype=cdt)
+    well_rate = np.zeros((nwell, nb), dtype=cdt)
     well_grad = []          # per well: (cells, dq/dlocal of shape (nperf, nb, L))
     for iw, w in enumerate(spec.wells):
         cells_w = np.asarray(w.cells, dtype=np.int64)
@@ -268,7 +272,7 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
                 w_res[iw] = (p_bh[iw] - target) if mode == 0 else -target
                 w_res_m[iw] = (abs(p_bh[iw]) + abs(target)) if mode == 0 else abs(target)
                 w_D[iw] = 1.0 if mode == 0 else 0.0
-                w_D_m[iw] = w_D[iw]
+                w_D_m[iw] = abs(w_D[iw])
             continue
         P = {key: val_.take(cells_w).embed(Lw, 0) for key, val_ in pn.items() if val_ is not None}
         WI = well_index(spec, w, lnk.take(cells_w)).embed(Lw, 0)
@@ -309,7 +313,7 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
                 w_res_m[iw] = abs(p_bh[iw]) + abs(target)
                 w_D[iw] = 1.0
                 w_D_m[iw] = 1.0
-                w_C.append(np.zeros((n_w, nb)))
+                w_C.append(np.zeros((n_w, nb), dtype=cdt))
                 w_C_m.append(np.zeros((n_w, nb)))
             else:
                 sgn = -1.0 if w.kind == 0 else 1.0
@@ -318,7 +322,7 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
                 w_res_m[iw] = q.m.sum() + abs(target)
                 w_D[iw] = sgn * q.g[:, L].sum()
                 w_D_m[iw] = q.gm[:, L].sum()
-                c_blk = np.zeros((n_w, nb))
+                c_blk = np.zeros((n_w, nb), dtype=cdt)
                 c_blk[:, :nv] = sgn * q.g[:, :nv]
                 c_mag = np.zeros((n_w, nb))
                 c_mag[:, :nv] = q.gm[:, :nv]

@@ -44,6 +44,11 @@ MUTATIONS = [
     ("blackoil.py", 'm_o = pr["phi"] * pr["S_o"] * pr["b_o"]', 'm_o = pr["phi"] * pr["S_w"] * pr["b_o"]'),
     ("blackoil.py", 's_w = clamp01((sw - swc) / (1.0 - swc - sorw))',
      's_w = clamp01((sw - swc) / (1.0 - swc))'),                                # Corey end point
+    ("dual.py", "g = self.g * o.v[:, None] + self.v[:, None] * o.g",
+     "g = self.g * o.v[:, None]"),                                              # product rule term
+    ("linearize.py", "return D(e, e[:, None] * a.g, ae, ae[:, None] * a.gm)",
+     "return D(e, a.g, ae, ae[:, None] * a.gm)"),                              # d exp(x) = exp(x) dx
+    ("dual.py", "dv = e * self.v ** (e - 1.0)", "dv = self.v ** (e - 1.0)"),   # power rule factor
 ]
 
 
@@ -224,7 +229,33 @@ def pin_buckley_leverett(lin, newton, bo):
     return bool(np.mean(np.abs(u[1] - ex)) < 0.04)
 
 
-PINS = [pin_mass_balance, pin_fd, pin_hydrostatic, pin_compressible_column, pin_capillary_direction,
+def pin_complex_step(lin, newton, bo):
+    g, s = W.tiny(2, 2, 2, seed=22)
+    o = run(lin, g, s)
+    A = dense(o)
+    M = np.abs(dense({"row_ptr": o["row_ptr"], "col_idx": o["col_idx"], "val": o["val_mag"]}))
+    N, nb, h = g.N, 3, 1e-30
+    for c in range(N):
+        for v in range(nb):
+            u = s.u_new.astype(complex).copy()
+            u[v, c] += 1j * h
+            col = lin.linearize(g, u, s.flag_new, s.u_old, s.flag_old, s.dt)["R"].ravel().imag / h
+            if np.any(np.abs(col - A[:, c * nb + v]) > 1e-13 * M[:, c * nb + v]):
+                return False
+    # the adjoint's ln k gradient (transmissibility and well index)
+    lam = np.random.default_rng(3).normal(size=(N, nb))
+    o = run(lin, g, s, mode="all", lam=lam)
+    for c in range(N):
+        gg = copy.deepcopy(g)
+        gg.lnk = np.asarray(gg.lnk, dtype=complex)
+        gg.lnk[c] += 1j * h
+        cs = np.sum(lam * run(lin, gg, s)["R"].imag) / h
+        if abs(cs - o["g_lnk"][c]) > 1e-13 * o["g_lnk_mag"][c]:
+            return False
+    return True
+
+
+PINS = [pin_mass_balance, pin_fd, pin_complex_step, pin_hydrostatic, pin_compressible_column, pin_capillary_direction,
         pin_tables, pin_laplacian, pin_surface_density_and_stone,
         pin_buckley_leverett]
 
