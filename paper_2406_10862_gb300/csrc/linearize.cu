@@ -40,80 +40,9 @@ constexpr int kInc = 49;    // shares handed over, 3 x (F 3 + dj 9)   49 .. 84
 // CellQ fields each block size reads (the two-phase path skips the gas and
 // dissolved-gas fields).
 template <int NB>
-__host__ __device__ constexpr bool q_used(int f) {
-  return NB == 3 || !(f == 2 || f == 4 || f == 9 || f == 10 || f == 11 || f == 18 || f >= 19);
-}
-// Number of CellQ fields a block size reads, and the field of staged row qi.
-template <int NB>
-__host__ __device__ constexpr int q_count() {
-  int n = 0;
-  for (int f = 0; f < kQ; ++f) n += q_used<NB>(f);
-  return n;
-}
-template <int NB>
-__host__ __device__ constexpr int q_field(int qi) {
-  for (int f = 0, k = 0; f < kQ; ++f)
-    if (q_used<NB>(f)) {
-      if (k == qi) return f;
-      ++k;
-    }
-  return kQ;
-}
-
-// ---------------------------------------------------------- staged windows
-// face_kernel stages, per tile of TPB cells starting at c0, three windows of
-// every CellQ field in shared memory: cells [c0, c0 + TPB + 1) (the tile and
-// its +x neighbours), [c0 + nx, c0 + nx + TPB) and [c0 + nxy, c0 + nxy + TPB)
-// (the +y and +z neighbours), each clamped to the grid.  Each window row is
-// one bulk asynchronous copy (the TMA unit) of a contiguous range of the
-// field-major scratch; all of a tile's copies complete on one mbarrier.  A
-// copy must start and end on 16-byte boundaries, so a row takes the window
-// rounded out to whole pairs of doubles (at most 2 more than its length)
-// and the reader skips the first double where the window starts odd.  The
-// rounded range never leaves the scratch: it ends at most one double past
-// field f's cell N - 1, and fields up to 24 of the 85 in use are staged.
-constexpr unsigned kFaceSpin = 1u << 20;
-
-template <int NB, int TPB>
-__host__ __device__ constexpr int face_row() { return TPB + 4; }   // doubles per staged row (16-byte multiple)
-template <int NB, int TPB>
-__host__ __device__ constexpr int face_smem_bytes() { return 3 * q_count<NB>() * face_row<NB, TPB>() * 8; }
-
-__device__ __forceinline__ bool mbar_wait_parity(unsigned bar, unsigned parity) {
-  for (unsigned it = 0; it < kFaceSpin; ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// Cells of window w (0: tile and +x, 1: +y, 2: +z) present in the grid.
-template <int TPB>
-__device__ __forceinline__ long long window_len(long long N, long long start, int w) {
-  const long long want = TPB + (w == 0), avail = N - start;
-  return avail <= 0 ? 0 : (want < avail ? want : avail);
-}
-
-template <int NB, int TPB>
-__device__ __forceinline__ void load_q_staged(const double* __restrict__ fsm, long long N, long long start, int w,
-                                              int l, CellQ& q) {
-  double* f = reinterpret_cast<double*>(&q);
-  constexpr int NQ = q_count<NB>(), S = face_row<NB, TPB>();
-  int qi = 0;
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    if (q_used<NB>(i)) {
-      f[i] = fsm[(w * NQ + qi) * S + (int)((i * N + start) & 1) + l];
-      ++qi;
-    } else {
-      f[i] = 0.0;
-    }
-  }
+__device__ __forceinline__ bool q_used(int f) {
+  if (NB == 3) return true;
+  return !(f == 2 || f == 4 || f == 9 || f == 10 || f == 11 || f == 18 || f >= 19);
 }
 
 template <int NB>
@@ -186,9 +115,8 @@ __device__ __forceinline__ void cell_body(const ModelArgs& M, const Table& T, lo
   }
 }
 
-template <int NB, int TPB>
-__device__ __forceinline__ void face_body(const ModelArgs& M, long long c, long long c0,
-                                          const double* __restrict__ fsm) {
+template <int NB>
+__device__ __forceinline__ void face_body(const ModelArgs& M, long long c) {
   constexpr int B2 = NB * NB;
   const Params& P = M.P;
   const long long N = P.N;
@@ -202,7 +130,7 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c, long 
   const bool hp[3] = {i + 1 < P.nx, j + 1 < P.ny, k + 1 < P.nz};
   const long long stride[3] = {1, P.nx, P.nxy};
   CellQ a;
-  load_q_staged<NB, TPB>(fsm, N, c0, 0, (int)(c - c0), a);
+  load_q<NB>(scr, N, c, a);
   double r[NB], dg[NB][NB];
 #pragma unroll
   for (int e = 0; e < NB; ++e) {
@@ -221,7 +149,7 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c, long 
     }
     const long long n = c + stride[d];
     CellQ b;
-    load_q_staged<NB, TPB>(fsm, N, c0 + stride[d] * (d > 0), d, (int)(c - c0) + (d == 0), b);
+    load_q<NB>(scr, N, n, b);
     FaceOut<NB> o;
     const double T = M.trans[d * N + c];
     if (d == 2) face_terms<NB, true>(T, -P.grav_dz, a, b, o);
@@ -335,59 +263,13 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) cell_kernel(TileList L, ModelA
 }
 
 template <int NB, int TPB>
-__global__ void __launch_bounds__(TPB, (NB == 3 ? 256 : 512) / TPB) face_kernel(TileList L, ModelArgs single) {
-  constexpr int NQ = q_count<NB>(), S = face_row<NB, TPB>();
-  extern __shared__ __align__(128) double fsm[];
-  __shared__ __align__(8) unsigned long long bar;
-  const unsigned ubar = (unsigned)__cvta_generic_to_shared(&bar);
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ubar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  unsigned parity = 0;
+__global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) face_kernel(TileList L, ModelArgs single) {
   for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
     int m;
     long long c0;
     const ModelArgs& M = tile_of<TPB>(L, single, t, m, c0);
-    const long long N = M.P.N;
-    const long long wstart[3] = {c0, c0 + M.P.nx, c0 + M.P.nxy};
-    if (threadIdx.x == 0) {            // arm the barrier with the tile's byte count
-      unsigned total = 0;
-      for (int w = 0; w < 3; ++w) {
-        const long long len = window_len<TPB>(N, wstart[w], w);
-        if (len == 0) continue;
-        for (int qi = 0; qi < NQ; ++qi) {
-          const long long g0 = q_field<NB>(qi) * N + wstart[w];
-          total += (unsigned)((((g0 + len + 1) & ~1ll) - (g0 & ~1ll)) * 8);
-        }
-      }
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ubar), "r"(total) : "memory");
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < 3 * NQ; j += TPB) {
-      const int w = j / NQ, qi = j - w * NQ;
-      const long long len = window_len<TPB>(N, wstart[w], w);
-      if (len == 0) continue;
-      const long long g0 = q_field<NB>(qi) * N + wstart[w];
-      const long long a = g0 & ~1ll;
-      const unsigned bytes = (unsigned)((((g0 + len + 1) & ~1ll) - a) * 8);
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-              (unsigned)__cvta_generic_to_shared(fsm + (w * NQ + qi) * S)),
-          "l"(M.scr + a), "r"(bytes), "r"(ubar)
-          : "memory");
-    }
-    const bool ok = mbar_wait_parity(ubar, parity);
-    if (__syncthreads_or(!ok)) {       // a copy that never lands: report, let it drain, stop
-      if (threadIdx.x == 0) atomicOr(M.status, kStatTimeout);
-      mbar_wait_parity(ubar, parity);
-      return;
-    }
-    parity ^= 1u;
     const long long c = c0 + threadIdx.x;
-    if (c < N) face_body<NB, TPB>(M, c, c0, fsm);
-    __syncthreads();                   // the windows are free before the next tile's copies
+    if (c < M.P.N) face_body<NB>(M, c);
   }
 }
 
@@ -405,28 +287,11 @@ __global__ void __launch_bounds__(TPB) assemble_kernel(TileList L, ModelArgs sin
 template <int NB, int TPB>
 void launch_stage(int stage, const TileList& L, const ModelArgs& single, int grid, cudaStream_t s) {
   if (stage == 0) cell_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
-  else if (stage == 1) face_kernel<NB, TPB><<<grid, TPB, face_smem_bytes<NB, TPB>(), s>>>(L, single);
+  else if (stage == 1) face_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
   else assemble_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
 }
 
 }  // namespace
-
-// The face kernel's staged windows take more than the default 48 KB of
-// shared memory; the attribute is set on the current device.
-cudaError_t configure_linearize_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(face_kernel<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       face_smem_bytes<3, 128>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(face_kernel<3, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             face_smem_bytes<3, 256>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(face_kernel<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             face_smem_bytes<2, 128>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(face_kernel<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             face_smem_bytes<2, 256>());
-  return e;
-}
 
 // Launches the three stages.  `lists[0]` / `lists[1]` are the tile lists for
 // 128 / 256 cells per tile; cfg picks, per stage, the tile size and the grid
@@ -483,7 +348,6 @@ namespace {
 cudaError_t launch_single(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
                           const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
                           double* face_flux, cudaStream_t s, const double* p_bh = nullptr, int no_acc = 0) {
-  if (((uintptr_t)scratch & 15) != 0) return cudaErrorMisalignedAddress;   // the staged copies need 16 bytes
   ModelArgs M = model_args(g, scratch, u_new, f_new, u_old, f_old, dt, res, val, face_flux);
   M.p_bh = p_bh;
   M.no_acc = no_acc;
