@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kBulkRows) spmv_bulk_kernel(Params P, const in
   }
   __syncthreads();                       // the barrier is initialised before anyone waits on it
   if (size > 0 && !bulk_wait(ubar)) {
-    if (threadIdx.x == 0) atomicOr(status, kStatTimeout);
+    atomicOr(status, kStatTimeout);      // every thread that gives up reports it: its rows stay unwritten
     bulk_wait(ubar);                     // the copy in flight gets one more bounded wait
     return;
   }
