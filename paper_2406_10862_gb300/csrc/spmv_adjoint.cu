@@ -200,9 +200,9 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const
 // of b1 B rounded up to 16 and the array size rounded down to 16, so source
 // (val must be 16-byte aligned), destination and size are 16-byte multiples
 // and the copy stays inside the array.  The one double an array of odd size
-// can have past e is read from global memory.  The wait is bounded: past
-// its limit the CTA records kStatTimeout, waits once more for its copy and
-// returns.
+// can have past e is read from global memory.  The wait is bounded: a
+// thread past its limit records kStatTimeout (reported by ocp_get_status as
+// OCP_ERR_TIMEOUT), waits once more for the copy in flight and returns.
 constexpr int kBulkRows = 128;
 constexpr unsigned kBulkSpin = 1u << 20;
 
