@@ -93,25 +93,41 @@ __global__ void pn_split_kernel(Params P, const Table* __restrict__ gT, const do
   elim[NB * N + c] = cr;
 }
 
+// The row's blocks are walked on the grid's 7-point pattern (neighbour
+// types -z, -y, -x, self, +x, +y, +z, the order of the stored columns), with
+// the row start in closed form: no dependent index loads, so every block's
+// gathers can be issued early, and the diagonal's extra terms are placed at
+// compile time.
 template <int NB>
-__global__ void pn_reduce_kernel(Params P, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                                 const double* __restrict__ d, const double* __restrict__ elim,
-                                 const double* __restrict__ pn_new, const double* __restrict__ pn_old, double scale,
-                                 double* __restrict__ res, double* __restrict__ val, double* __restrict__ res4,
-                                 double* __restrict__ val4) {
+__global__ void __launch_bounds__(128) pn_reduce_kernel(Params P, const double* __restrict__ d,
+                                                        const double* __restrict__ elim,
+                                                        const double* __restrict__ pn_new,
+                                                        const double* __restrict__ pn_old, double scale,
+                                                        double* __restrict__ res, double* __restrict__ val,
+                                                        double* __restrict__ res4, double* __restrict__ val4) {
   using Lo = PnLayout<NB>;
   constexpr int L = NB + 1;
   const long long N = P.N;
   const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= N) return;
+  int ri, rj, rk;
+  cell_ijk(P, r, ri, rj, rk);
+  const bool has[7] = {rk > 0, rj > 0, ri > 0, true, ri + 1 < P.nx, rj + 1 < P.ny, rk + 1 < P.nz};
+  const long long off[7] = {-P.nxy, -P.nx, -1, 0, 1, P.nx, P.nxy};
+  const long long s0 = row_start_ijk(P, r, ri, rj, rk);
   double rr[NB];
   for (int e = 0; e < NB; ++e) rr[e] = fma(pn_new[(e + 1) * N + r] - pn_old[(e + 1) * N + r], scale, res[r * NB + e]);
   if (res4) {
     for (int e = 0; e < NB; ++e) res4[r * L + e] = rr[e];
     res4[r * L + NB] = d[(Lo::kA + L) * N + r];
   }
-  for (int s = row_ptr[r]; s < row_ptr[r + 1]; ++s) {
-    const long long c = col_idx[s];
+  int slot = 0;
+#pragma unroll
+  for (int t = 0; t < 7; ++t) {
+    if (!has[t]) continue;
+    const long long s = s0 + slot;
+    ++slot;
+    const long long c = r + off[t];
     double B[NB][NB];
     for (int e = 0; e < NB; ++e)
       for (int v = 0; v < NB; ++v) B[e][v] = val[(long long)s * NB * NB + e * NB + v];
@@ -127,26 +143,26 @@ __global__ void pn_reduce_kernel(Params P, const int32_t* __restrict__ row_ptr, 
       double* b4 = val4 + (long long)s * L * L;
       for (int e = 0; e < NB; ++e)
         for (int k = 0; k < L; ++k) {
-          double t = 0.0;
-          for (int i = 0; i < NB; ++i) t = fma(B[e][i], Mc[i][k], t);
-          b4[e * L + k] = (c == r && k == e + 1) ? t + scale : t;
+          double acc = 0.0;
+          for (int i = 0; i < NB; ++i) acc = fma(B[e][i], Mc[i][k], acc);
+          b4[e * L + k] = (t == 3 && k == e + 1) ? acc + scale : acc;
         }
-      for (int k = 0; k < L; ++k) b4[NB * L + k] = (c == r) ? d[(Lo::kA + k) * N + r] : 0.0;
+      for (int k = 0; k < L; ++k) b4[NB * L + k] = (t == 3) ? d[(Lo::kA + k) * N + r] : 0.0;
     }
     for (int e = 0; e < NB; ++e) {
       double corr = 0.0;
       for (int i = 0; i < NB; ++i) corr = fma(B[e][i], tc[i], corr);
       rr[e] -= corr;
       for (int j = 0; j < NB; ++j) {
-        double t = 0.0;
-        for (int i = 0; i < NB; ++i) t = fma(B[e][i], Tc[i][j], t);
-        if (c == r) {
+        double acc = 0.0;
+        for (int i = 0; i < NB; ++i) acc = fma(B[e][i], Tc[i][j], acc);
+        if (t == 3) {
           // accumulation (N_e - N_e,old) V/dt: water row through the
           // eliminated N_w, the other rows on their own amounts
-          if (e == 0) t = fma(-elim[j * N + r], scale, t);
-          else if (j == e) t += scale;
+          if (e == 0) acc = fma(-elim[j * N + r], scale, acc);
+          else if (j == e) acc += scale;
         }
-        val[(long long)s * NB * NB + e * NB + j] = t;
+        val[s * NB * NB + e * NB + j] = acc;
       }
     }
   }
@@ -264,10 +280,10 @@ ocp_status ocp_linearize_pn(ocp_grid* g, const double* pn_new, const double* pn_
     e = launch_linearize(g, unat, g->d_pn_flag, unat, g->d_pn_flag, dt, residual, bsr_val, nullptr, s, nullptr, 1);
   if (e == cudaSuccess) {
     if (nb == 3)
-      pn_reduce_kernel<3><<<nblk(N, 128), 128, 0, s>>>(g->prm, g->d_row_ptr, g->d_col_idx, g->d_pn, elim, pn_new,
+      pn_reduce_kernel<3><<<nblk(N, 128), 128, 0, s>>>(g->prm, g->d_pn, elim, pn_new,
                                                        pn_old, scale, residual, bsr_val, residual_full, bsr_val_full);
     else
-      pn_reduce_kernel<2><<<nblk(N, 128), 128, 0, s>>>(g->prm, g->d_row_ptr, g->d_col_idx, g->d_pn, elim, pn_new,
+      pn_reduce_kernel<2><<<nblk(N, 128), 128, 0, s>>>(g->prm, g->d_pn, elim, pn_new,
                                                        pn_old, scale, residual, bsr_val, residual_full, bsr_val_full);
     e = cudaGetLastError();
   }
