@@ -2,9 +2,11 @@
 //
 // spmv_grid_kernel  y = alpha A x + beta y on the grid's 7-point block pattern
 //                   (the kernel the linear solver iterates on, Sec. 3.3.3);
-// spmv_kernel<T>    the transposed product, gathered through the mirror map
-//                   (block (c, n) <-> block (n, c)) so that every output row is
-//                   owned by one thread and no atomics are needed;
+// spmv_grid_t_kernel the transposed product: every output row gathers the
+//                   blocks (n, c) of its column, located in closed form, so
+//                   that it is owned by one thread and no atomics are needed;
+// spmv_bulk_kernel  y = alpha A x + beta y for 2x2 and 1x1 blocks with the
+//                   matrix slices staged by bulk asynchronous copies;
 // vjp_kernel        lambda^T dR/d(u_new, u_old, ln k, phi) of the residual of
 //                   eqs. 1, 2 and 4: J^T lambda through the mirror map, the
 //                   transmissibility and well-index terms from the stored face
@@ -87,42 +89,6 @@ __global__ void setup_kernel(Params P, const double* __restrict__ lnk, double dx
 
 // ------------------------------------------------------------------ SpMV
 // mode 0: y = A x;  1: y = alpha A x;  2: y = alpha A x + beta y
-template <int NB, bool TRANS>
-__global__ void __launch_bounds__(256) spmv_kernel(long long N, const int32_t* __restrict__ row_ptr,
-                                                   const int32_t* __restrict__ col_idx,
-                                                   const int32_t* __restrict__ mirror,
-                                                   const double* __restrict__ val, double alpha,
-                                                   const double* __restrict__ x, double beta,
-                                                   double* __restrict__ y, int mode) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= N) return;
-  double acc[NB];
-#pragma unroll
-  for (int e = 0; e < NB; ++e) acc[e] = 0.0;
-  const int s0 = row_ptr[c], s1 = row_ptr[c + 1];
-  for (int s = s0; s < s1; ++s) {
-    const long long n = col_idx[s];
-    const double* blk = val + (long long)(TRANS ? mirror[s] : s) * NB * NB;
-    double xv[NB];
-#pragma unroll
-    for (int v = 0; v < NB; ++v) xv[v] = x[n * NB + v];
-#pragma unroll
-    for (int e = 0; e < NB; ++e)
-#pragma unroll
-      for (int v = 0; v < NB; ++v) {
-        if (TRANS) acc[e] = fma(blk[v * NB + e], xv[v], acc[e]);
-        else acc[e] = fma(blk[e * NB + v], xv[v], acc[e]);
-      }
-  }
-#pragma unroll
-  for (int e = 0; e < NB; ++e) {
-    double o = acc[e];
-    if (mode >= 1) o = alpha * o;
-    if (mode == 2) o = fma(beta, y[c * NB + e], o);
-    y[c * NB + e] = o;
-  }
-}
-
 // Product on the grid's own pattern, one thread per block row.  The FP64
 // FMAs (NB*NB per block) are the binding resource on GB300, so the kernel
 // is arranged to keep them fed: the columns come from the 7-point structure
@@ -181,6 +147,54 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const
     if (mode >= 1) o = alpha * o;
     if (mode == 2) o = fma(beta, y[c * NB + e], o);
     y[c * NB + e] = o;
+  }
+}
+
+// Transposed product on the grid's pattern, one thread per output row c:
+// y_c = sum over the stored blocks (n, c) of A(n, c)^T x_n, with the blocks
+// visited in the order of row c's columns (neighbour types -z .. +z).  Block
+// (n, c) lies in row n at the slot of the opposite type 6 - t: n's row start
+// in closed form plus the number of n's neighbour types before 6 - t, so no
+// index is loaded (no col_idx, no mirror).  The FMAs and their order are
+// those of the gather through the mirror map.
+template <int NB>
+__global__ void __launch_bounds__(kSpmvThreads) spmv_grid_t_kernel(Params P, const double* __restrict__ val,
+                                                                   double alpha, const double* __restrict__ x,
+                                                                   double beta, double* __restrict__ y, int mode) {
+  constexpr int B2 = NB * NB;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.N) return;
+  int ci, cj, ck;
+  cell_ijk(P, c, ci, cj, ck);
+  const bool has[7] = {ck > 0, cj > 0, ci > 0, true, ci + 1 < P.nx, cj + 1 < P.ny, ck + 1 < P.nz};
+  const long long off[7] = {-P.nxy, -P.nx, -1, 0, 1, P.nx, P.nxy};
+  double acc[NB];
+#pragma unroll
+  for (int v = 0; v < NB; ++v) acc[v] = 0.0;
+#pragma unroll
+  for (int t = 0; t < 7; ++t) {
+    if (!has[t]) continue;
+    const long long n = c + off[t];
+    // (i, j, k) of n and the slot of type 6 - t in its row
+    const int ni = ci + (t == 4) - (t == 2), nj = cj + (t == 5) - (t == 1), nk = ck + (t == 6) - (t == 0);
+    const bool hn[6] = {nk > 0, nj > 0, ni > 0, true, ni + 1 < P.nx, nj + 1 < P.ny};
+    int sn = 0;
+#pragma unroll
+    for (int u = 0; u < 6 - t; ++u) sn += hn[u];
+    const double* blk = val + (row_start_ijk(P, n, ni, nj, nk) + sn) * B2;
+#pragma unroll
+    for (int e = 0; e < NB; ++e) {
+      const double l = x[n * NB + e];
+#pragma unroll
+      for (int v = 0; v < NB; ++v) acc[v] = fma(__ldg(blk + e * NB + v), l, acc[v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NB; ++v) {
+    double o = acc[v];
+    if (mode >= 1) o = alpha * o;
+    if (mode == 2) o = fma(beta, y[c * NB + v], o);
+    y[c * NB + v] = o;
   }
 }
 
@@ -463,7 +477,6 @@ cudaError_t launch_setup(ocp_grid* g, const double* d_lnk, double dx, double dy,
 cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, const double* x, double beta,
                         double* y, int transpose, cudaStream_t s, int nbs) {
   const long long N = g->prm.N;
-  const unsigned blocks = (unsigned)((N + 255) / 256);
   const int mode = (beta != 0.0) ? 2 : (alpha != 1.0 ? 1 : 0);
   const unsigned gblocks = (unsigned)((N + kSpmvThreads - 1) / kSpmvThreads);
   const int nb = nbs > 0 ? nbs : g->prm.nb;
@@ -473,14 +486,14 @@ cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, cons
   const bool bulk = ((uintptr_t)val & 15) == 0;
   const unsigned bblocks = (unsigned)((N + kBulkRows - 1) / kBulkRows);
   if (nb == 3) {
-    if (transpose) spmv_kernel<3, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+    if (transpose) spmv_grid_t_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode);
     else spmv_grid_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
   } else if (nb == 2) {
-    if (transpose) spmv_kernel<2, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+    if (transpose) spmv_grid_t_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode);
     else if (bulk) spmv_bulk_kernel<2><<<bblocks, kBulkRows, bulk_smem_bytes<2>(), s>>>(g->prm, g->d_row_ptr, g->nnzb, val, alpha, x, beta, y, mode, g->d_status);
     else spmv_grid_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
   } else {
-    if (transpose) spmv_kernel<1, true><<<blocks, 256, 0, s>>>(N, g->d_row_ptr, g->d_col_idx, g->d_mirror, val, alpha, x, beta, y, mode);
+    if (transpose) spmv_grid_t_kernel<1><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode);
     else if (bulk) spmv_bulk_kernel<1><<<bblocks, kBulkRows, bulk_smem_bytes<1>(), s>>>(g->prm, g->d_row_ptr, g->nnzb, val, alpha, x, beta, y, mode, g->d_status);
     else spmv_grid_kernel<1><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
   }
