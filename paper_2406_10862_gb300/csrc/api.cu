@@ -48,7 +48,6 @@ void free_grid(ocp_grid* g) {
   cudaFree(g->d_table);
   cudaFree(g->d_row_ptr);
   cudaFree(g->d_col_idx);
-  cudaFree(g->d_mirror);
   cudaFree(g->d_trans);
   cudaFree(g->d_wlnk);
   cudaFree(g->d_phi);
@@ -257,7 +256,6 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   OCP_ALLOC(g->d_table, sizeof(ocp::Table));
   OCP_ALLOC(g->d_row_ptr, sizeof(int32_t) * (N + 1));
   OCP_ALLOC(g->d_col_idx, sizeof(int32_t) * g->nnzb);
-  OCP_ALLOC(g->d_mirror, sizeof(int32_t) * g->nnzb);
   OCP_ALLOC(g->d_trans, sizeof(double) * 3 * N);
   OCP_ALLOC(g->d_wlnk, sizeof(double) * 6 * N);
   OCP_ALLOC(g->d_phi, sizeof(double) * N);

@@ -91,7 +91,6 @@ struct ocp_grid {
   int64_t nnzb;
   int32_t* d_row_ptr;
   int32_t* d_col_idx;
-  int32_t* d_mirror;         // index of block (col,row) for block (row,col)
   double* d_trans;           // [3][N] transmissibility of the +x,+y,+z face (0 outside)
   double* d_wlnk;            // [3][N] dlnT/dln k_i of the +face for its lower cell
   double* d_phi;             // [N] reference porosity

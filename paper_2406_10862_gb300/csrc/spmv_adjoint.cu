@@ -8,12 +8,12 @@
 // spmv_bulk_kernel  y = alpha A x + beta y for 2x2 and 1x1 blocks with the
 //                   matrix slices staged by bulk asynchronous copies;
 // vjp_kernel        lambda^T dR/d(u_new, u_old, ln k, phi) of the residual of
-//                   eqs. 1, 2 and 4: J^T lambda through the mirror map, the
+//                   eqs. 1, 2 and 4: J^T lambda with the column's blocks found in closed form, the
 //                   transmissibility and well-index terms from the stored face
 //                   fluxes (T and WI are linear in the fluxes), and the
 //                   accumulation terms recomputed from the two states.
-// setup_kernel      per-grid geometry: transmissibilities, their ln k weights,
-//                   the block-CSR pattern and the mirror map.
+// setup_kernel      per-grid geometry: transmissibilities, their ln k weights
+//                   and the block-CSR pattern.
 // well_rate_kernel  surface rates of each well (one thread per well, its
 //                   perforations summed in order).
 #include "ocp_internal.cuh"
@@ -42,8 +42,7 @@ __device__ __forceinline__ long long row_start(const Params& P, long long c) {
 
 __global__ void setup_kernel(Params P, const double* __restrict__ lnk, double dx, double dy, double dz,
                              double kzr, double* __restrict__ trans, double* __restrict__ wlnk,
-                             int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
-                             int32_t* __restrict__ mirror) {
+                             int32_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx) {
   const long long N = P.N;
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= N) return;
@@ -77,12 +76,6 @@ __global__ void setup_kernel(Params P, const double* __restrict__ lnk, double dx
     if (!has[t]) continue;
     const long long n = c + off[t];
     col_idx[start + s] = (int32_t)n;
-    // slot of the opposite type (6 - t) in row n
-    bool hn[7];
-    neighbours(P, n, hn);
-    int sn = 0;
-    for (int u = 0; u < 6 - t; ++u) sn += hn[u];
-    mirror[start + s] = (int32_t)(row_start(P, n) + sn);
     ++s;
   }
 }
@@ -155,8 +148,8 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const
 // visited in the order of row c's columns (neighbour types -z .. +z).  Block
 // (n, c) lies in row n at the slot of the opposite type 6 - t: n's row start
 // in closed form plus the number of n's neighbour types before 6 - t, so no
-// index is loaded (no col_idx, no mirror).  The FMAs and their order are
-// those of the gather through the mirror map.
+// index is loaded.  The FMAs run in the order of a gather of row c's
+// columns: block by block, each block's rows in turn.
 template <int NB>
 __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_t_kernel(Params P, const double* __restrict__ val,
                                                                    double alpha, const double* __restrict__ x,
@@ -329,9 +322,6 @@ __global__ void __launch_bounds__(256) vjp_kernel(Params P, const Table* __restr
                                                   const double* __restrict__ u_old,
                                                   const int8_t* __restrict__ f_old,
                                                   const double* __restrict__ phi,
-                                                  const int32_t* __restrict__ row_ptr,
-                                                  const int32_t* __restrict__ col_idx,
-                                                  const int32_t* __restrict__ mirror,
                                                   const double* __restrict__ val,
                                                   const double* __restrict__ face_flux,
                                                   const double* __restrict__ wlnk,
@@ -352,12 +342,25 @@ __global__ void __launch_bounds__(256) vjp_kernel(Params P, const Table* __restr
   for (int e = 0; e < NB; ++e) lc[e] = lam[c * NB + e];
 
   if (g_unew) {
+    // J^T lambda: the blocks (n, c) of column c, found in closed form as in
+    // spmv_grid_t_kernel, in the order of row c's columns
+    int ci, cj, ck;
+    cell_ijk(P, c, ci, cj, ck);
+    const bool hc[7] = {ck > 0, cj > 0, ci > 0, true, ci + 1 < P.nx, cj + 1 < P.ny, ck + 1 < P.nz};
+    const long long off[7] = {-P.nxy, -P.nx, -1, 0, 1, P.nx, P.nxy};
     double acc[NB];
 #pragma unroll
     for (int v = 0; v < NB; ++v) acc[v] = 0.0;
-    for (int s = row_ptr[c]; s < row_ptr[c + 1]; ++s) {
-      const long long n = col_idx[s];
-      const double* blk = val + (long long)mirror[s] * NB * NB;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+      if (!hc[t]) continue;
+      const long long n = c + off[t];
+      const int ni = ci + (t == 4) - (t == 2), nj = cj + (t == 5) - (t == 1), nk = ck + (t == 6) - (t == 0);
+      const bool hn[6] = {nk > 0, nj > 0, ni > 0, true, ni + 1 < P.nx, nj + 1 < P.ny};
+      int sn = 0;
+#pragma unroll
+      for (int u = 0; u < 6 - t; ++u) sn += hn[u];
+      const double* blk = val + (row_start_ijk(P, n, ni, nj, nk) + sn) * NB * NB;
 #pragma unroll
       for (int e = 0; e < NB; ++e) {
         const double l = lam[n * NB + e];
@@ -470,7 +473,7 @@ cudaError_t launch_setup(ocp_grid* g, const double* d_lnk, double dx, double dy,
   const Params& P = g->prm;
   const unsigned blocks = (unsigned)((P.N + 255) / 256);
   setup_kernel<<<blocks, 256, 0, s>>>(P, d_lnk, dx, dy, dz, kz_over_kx, g->d_trans, g->d_wlnk,
-                                      g->d_row_ptr, g->d_col_idx, g->d_mirror);
+                                      g->d_row_ptr, g->d_col_idx);
   return cudaGetLastError();
 }
 
@@ -508,13 +511,13 @@ cudaError_t launch_vjp(const ocp_grid* g, const double* u_new, const int8_t* f_n
   const unsigned blocks = (unsigned)((P.N + 255) / 256);
   const double scale = P.vol_rb / dt;
   if (P.nb == 3)
-    vjp_kernel<3><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, g->d_row_ptr,
-                                         g->d_col_idx, g->d_mirror, val, face_flux, g->d_wlnk, g->d_perf_of_cell,
-                                         g->d_perf, scale, lam, g_unew, g_uold, g_lnk, g_phi);
+    vjp_kernel<3><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, val, face_flux,
+                                         g->d_wlnk, g->d_perf_of_cell, g->d_perf, scale, lam, g_unew, g_uold,
+                                         g_lnk, g_phi);
   else
-    vjp_kernel<2><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, g->d_row_ptr,
-                                         g->d_col_idx, g->d_mirror, val, face_flux, g->d_wlnk, g->d_perf_of_cell,
-                                         g->d_perf, scale, lam, g_unew, g_uold, g_lnk, g_phi);
+    vjp_kernel<2><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, val, face_flux,
+                                         g->d_wlnk, g->d_perf_of_cell, g->d_perf, scale, lam, g_unew, g_uold,
+                                         g_lnk, g_phi);
   return cudaGetLastError();
 }
 
