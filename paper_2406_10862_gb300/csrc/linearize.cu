@@ -123,7 +123,6 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c) {
   double* __restrict__ scr = M.scr;
   double* __restrict__ val = M.val;
   double* __restrict__ face_flux = M.face_flux;
-  const int32_t* __restrict__ row_ptr = M.row_ptr;
   int i, j, k;
   cell_ijk(P, c, i, j, k);
   const bool hm[3] = {i > 0, j > 0, k > 0};
@@ -138,7 +137,7 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c) {
 #pragma unroll
     for (int v = 0; v < NB; ++v) dg[e][v] = scr[(kSelf + 3 + 3 * e + v) * N + c];
   }
-  const long long row0 = row_ptr[c];
+  const long long row0 = row_start_ijk(P, c, i, j, k);   // the row pointers in closed form: no loads
   int slot = (int)hm[0] + (int)hm[1] + (int)hm[2] + 1;   // first + block of this row
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
@@ -168,7 +167,7 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c) {
     ++slot;
     // the + neighbour's row: its block of this cell, and its share
     const int slot_n = (d == 0) ? ((int)hm[2] + (int)hm[1]) : (d == 1 ? (int)hm[2] : 0);
-    double* nblk = val + ((long long)row_ptr[n] + slot_n) * B2;
+    double* nblk = val + (row_start_ijk(P, n, i + (d == 0), j + (d == 1), k + (d == 2)) + slot_n) * B2;
     const int base = kInc + 12 * d;
 #pragma unroll
     for (int e = 0; e < NB; ++e) {
@@ -215,7 +214,7 @@ __device__ __forceinline__ void assemble_body(const ModelArgs& M, long long c) {
       for (int v = 0; v < NB; ++v) dg[e][v] -= scr[(base + 3 + 3 * e + v) * N + c];
     }
   }
-  double* out = M.val + ((long long)M.row_ptr[c] + (int)hm[0] + (int)hm[1] + (int)hm[2]) * NB * NB;
+  double* out = M.val + (row_start_ijk(P, c, i, j, k) + (int)hm[0] + (int)hm[1] + (int)hm[2]) * NB * NB;
   bool ok = true;
 #pragma unroll
   for (int e = 0; e < NB; ++e) {
