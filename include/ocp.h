@@ -155,7 +155,11 @@ ocp_status ocp_linearize_noalloc(ocp_grid* grid, const double* u_new, const int8
  * y = alpha * A x + beta * y, or with transpose != 0, y = alpha * A^T x +
  * beta * y.  A is bsr_val on the grid's pattern; x and y are block-
  * interleaved [nb*N] device vectors and must not overlap.  beta == 0 does
- * not read y (so y may hold NaNs). */
+ * not read y (so y may hold NaNs).  With 2x2 blocks and a 16-byte aligned
+ * bsr_val the product stages the matrix through the copy engine; any other
+ * alignment takes a register path with bit-identical results.  The staged
+ * path's waits are bounded: one that expires leaves its rows unwritten and
+ * makes ocp_get_status return OCP_ERR_TIMEOUT. */
 ocp_status ocp_bsr_spmv(const ocp_grid* grid, const double* bsr_val, double alpha, const double* x,
                         double beta, double* y, int transpose, void* cuda_stream);
 
