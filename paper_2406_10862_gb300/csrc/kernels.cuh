@@ -29,8 +29,11 @@ struct WellSchur {
 };
 // mode 0: out += alpha bs (d^-1 (cs . in)); 1: out += alpha bs (d^-1 bw);
 // 2: xw = d^-1 (bw - cs . in)
+// skip: when not null, the kernels return at once if *skip != 0 (a solver's
+// done flag, so that the iterations left in a replayed graph cost nothing).
 cudaError_t launch_well_schur(const ocp_grid* g, const WellSchur& ws, int mode, double alpha, const double* in,
-                              double* out, const double* bw, double* xw, cudaStream_t s);
+                              double* out, const double* bw, double* xw, cudaStream_t s,
+                              const double* skip = nullptr);
 // Left block-Jacobi BiCGSTAB on A (ws == nullptr) or on the Schur complement
 // A - bs d^-1 cs of the well unknowns.
 // nbs: block size of the system (0: the grid's; 1: a scalar system on the
@@ -44,7 +47,7 @@ ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, co
                      const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
                      double* face_flux);
 cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, const double* x, double beta,
-                        double* y, int transpose, cudaStream_t s, int nbs = 0);
+                        double* y, int transpose, cudaStream_t s, int nbs = 0, const double* skip = nullptr);
 cudaError_t launch_vjp(const ocp_grid* g, const double* u_new, const int8_t* f_new, const double* u_old,
                        const int8_t* f_old, double dt, const double* val, const double* face_flux,
                        const double* lam, double* g_unew, double* g_uold, double* g_lnk, double* g_phi,

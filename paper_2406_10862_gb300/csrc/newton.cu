@@ -26,8 +26,10 @@ constexpr int kRedThreads = 256;
 // S_DONE, S_ITER, S_TARGET, S_MAXIT drive the device-side iteration control
 enum {
   S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_R0V, S_TS, S_TT, S_RR, S_BB, S_FLAG, S_TMP,
-  S_DONE, S_ITER, S_TARGET, S_MAXIT, S_COUNT
+  S_DONE, S_ITER, S_TARGET, S_MAXIT, S_TICKET, S_COUNT
 };
+// S_TICKET holds a 64-bit counter (not a double): the CTAs of a fused step
+// count themselves in, and the last one finishes the step's reductions.
 constexpr int kItersPerGraph = 8;     // BiCGSTAB iterations per graph replay
 
 __global__ void __launch_bounds__(kRedThreads) dot_partial(long long n, const double* __restrict__ a,
@@ -81,21 +83,6 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], double* __restri
     for (int q = 0; q < NV; ++q) part[q * kRedBlocks + blockIdx.x] = sh[q][0];
 }
 
-__device__ __forceinline__ double block_total(const double* __restrict__ part) {
-  __shared__ double sh[kRedThreads];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) s += part[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  const double t = sh[0];
-  __syncthreads();
-  return t;
-}
-
 // element i of the block-Jacobi product D^-1 z (the order of bj_apply_kernel)
 template <int NB>
 __device__ __forceinline__ double bj_elem(const double* __restrict__ dinv, const double* __restrict__ z, long long i) {
@@ -107,82 +94,33 @@ __device__ __forceinline__ double bj_elem(const double* __restrict__ dinv, const
   return s;
 }
 
-// v = D^-1 z and the partials of r0 . v
-template <int NB>
-__global__ void __launch_bounds__(kRedThreads) apply_dot(long long n, const double* __restrict__ dinv,
-                                                          const double* __restrict__ z, double* __restrict__ v,
-                                                          const double* __restrict__ r0, const double* __restrict__ sc,
-                                                          double* __restrict__ part) {
-  if (sc[S_DONE] != 0.0) return;
-  double acc[1] = {0.0};
-  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
-    const double x = bj_elem<NB>(dinv, z, i);
-    v[i] = x;
-    acc[0] = fma(r0[i], x, acc[0]);
-  }
-  block_partials<1>(acc, part);
-}
-
-// t = D^-1 z and the partials of t . s and t . t
-template <int NB>
-__global__ void __launch_bounds__(kRedThreads) apply_dot2(long long n, const double* __restrict__ dinv,
-                                                           const double* __restrict__ z, double* __restrict__ t,
-                                                           const double* __restrict__ sv, const double* __restrict__ sc,
-                                                           double* __restrict__ part) {
-  if (sc[S_DONE] != 0.0) return;
-  double acc[2] = {0.0, 0.0};
-  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
-    const double x = bj_elem<NB>(dinv, z, i);
-    t[i] = x;
-    acc[0] = fma(x, sv[i], acc[0]);
-    acc[1] = fma(x, x, acc[1]);
-  }
-  block_partials<2>(acc, part);
-}
-
-// x += alpha p + omega s, r = s - omega t, and the partials of r . r and r0 . r
-__global__ void __launch_bounds__(kRedThreads) upd_xr_dot(long long n, double* __restrict__ x,
-                                                           const double* __restrict__ p, const double* __restrict__ sv,
-                                                           double* __restrict__ r, const double* __restrict__ t,
-                                                           const double* __restrict__ r0, const double* __restrict__ sc,
-                                                           double* __restrict__ part) {
-  if (sc[S_DONE] != 0.0) return;
-  const double al = sc[S_ALPHA], om = sc[S_OMEGA];
-  double acc[2] = {0.0, 0.0};
-  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
-    x[i] = fma(om, sv[i], fma(al, p[i], x[i]));
-    const double ri = fma(-om, t[i], sv[i]);
-    r[i] = ri;
-    acc[0] = fma(ri, ri, acc[0]);
-    acc[1] = fma(r0[i], ri, acc[1]);
-  }
-  block_partials<2>(acc, part);
-}
-
-// the partials of a1 . b1 and a2 . b2 (start of the iteration)
-__global__ void __launch_bounds__(kRedThreads) dot2_partial(long long n, const double* __restrict__ a1,
-                                                             const double* __restrict__ b1,
-                                                             const double* __restrict__ a2,
-                                                             const double* __restrict__ b2, double* __restrict__ part) {
-  double acc[2] = {0.0, 0.0};
-  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
-    acc[0] = fma(a1[i], b1[i], acc[0]);
-    acc[1] = fma(a2[i], b2[i], acc[1]);
-  }
-  block_partials<2>(acc, part);
-}
-
-// Totals and the scalar step after them (one CTA; thread 0 writes):
+// Totals and the scalar step after them:
 //   kFinAlpha: r0.v -> alpha;  kFinOmega: t.s, t.t -> omega;
 //   kFinRrRho: r.r -> the loop's test for the next iteration (S_DONE or
 //   S_ITER + 1), then r0.r -> rho and beta.
 enum { kFinAlpha = 0, kFinOmega = 1, kFinRrRho = 2 };
 
+// The totals of the partials (the order and tree of dot_final), read from
+// L2: in the fused kernels other CTAs wrote them moments before.
+__device__ __forceinline__ double block_total_cg(const double* part) {
+  __shared__ double sh[kRedThreads];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) s += __ldcg(part + i);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double t = sh[0];
+  __syncthreads();
+  return t;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kRedThreads) fin_kernel(const double* __restrict__ part, double* __restrict__ sc) {
-  if (sc[S_DONE] != 0.0) return;
-  const double a = block_total(part);
-  const double b = (MODE == kFinAlpha) ? 0.0 : block_total(part + kRedBlocks);
+__device__ __forceinline__ void finish(const double* part, double* sc) {
+  const double a = block_total_cg(part);
+  const double b = (MODE == kFinAlpha) ? 0.0 : block_total_cg(part + kRedBlocks);
   if (threadIdx.x != 0) return;
   if constexpr (MODE == kFinAlpha) {
     sc[S_R0V] = a;
@@ -208,9 +146,105 @@ __global__ void __launch_bounds__(kRedThreads) fin_kernel(const double* __restri
   }
 }
 
+// Every CTA of a fused step takes a ticket after writing its partials; the
+// one that takes the last ticket has seen all of them written (each CTA
+// fences before its ticket) and finishes the step, then resets the counter.
+// The CTAs read every scalar they need before taking their tickets.
+template <int MODE>
+__device__ __forceinline__ void last_cta_finishes(const double* part, double* sc) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long prev = atomicAdd(reinterpret_cast<unsigned long long*>(sc + S_TICKET), 1ull);
+    last = prev == (unsigned long long)(kRedBlocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  finish<MODE>(part, sc);
+  if (threadIdx.x == 0) *reinterpret_cast<unsigned long long*>(sc + S_TICKET) = 0ull;
+}
+
+// v = D^-1 z, the partials of r0 . v, then alpha
+template <int NB>
+__global__ void __launch_bounds__(kRedThreads) apply_dot(long long n, const double* __restrict__ dinv,
+                                                          const double* __restrict__ z, double* __restrict__ v,
+                                                          const double* __restrict__ r0, double* sc,
+                                                          double* __restrict__ part) {
+  if (sc[S_DONE] != 0.0) return;
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
+    const double x = bj_elem<NB>(dinv, z, i);
+    v[i] = x;
+    acc[0] = fma(r0[i], x, acc[0]);
+  }
+  block_partials<1>(acc, part);
+  last_cta_finishes<kFinAlpha>(part, sc);
+}
+
+// t = D^-1 z, the partials of t . s and t . t, then omega
+template <int NB>
+__global__ void __launch_bounds__(kRedThreads) apply_dot2(long long n, const double* __restrict__ dinv,
+                                                           const double* __restrict__ z, double* __restrict__ t,
+                                                           const double* __restrict__ sv, double* sc,
+                                                           double* __restrict__ part) {
+  if (sc[S_DONE] != 0.0) return;
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
+    const double x = bj_elem<NB>(dinv, z, i);
+    t[i] = x;
+    acc[0] = fma(x, sv[i], acc[0]);
+    acc[1] = fma(x, x, acc[1]);
+  }
+  block_partials<2>(acc, part);
+  last_cta_finishes<kFinOmega>(part, sc);
+}
+
+// x += alpha p + omega s, r = s - omega t, the partials of r . r and r0 . r,
+// then the loop's test, rho and beta
+__global__ void __launch_bounds__(kRedThreads) upd_xr_dot(long long n, double* __restrict__ x,
+                                                           const double* __restrict__ p, const double* __restrict__ sv,
+                                                           double* __restrict__ r, const double* __restrict__ t,
+                                                           const double* __restrict__ r0, double* sc,
+                                                           double* __restrict__ part) {
+  if (sc[S_DONE] != 0.0) return;
+  const double al = sc[S_ALPHA], om = sc[S_OMEGA];
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
+    x[i] = fma(om, sv[i], fma(al, p[i], x[i]));
+    const double ri = fma(-om, t[i], sv[i]);
+    r[i] = ri;
+    acc[0] = fma(ri, ri, acc[0]);
+    acc[1] = fma(r0[i], ri, acc[1]);
+  }
+  block_partials<2>(acc, part);
+  last_cta_finishes<kFinRrRho>(part, sc);
+}
+
+// the partials of a1 . b1 and a2 . b2 (start of the iteration)
+__global__ void __launch_bounds__(kRedThreads) dot2_partial(long long n, const double* __restrict__ a1,
+                                                             const double* __restrict__ b1,
+                                                             const double* __restrict__ a2,
+                                                             const double* __restrict__ b2, double* __restrict__ part) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)kRedThreads + threadIdx.x; i < n; i += (long long)kRedBlocks * kRedThreads) {
+    acc[0] = fma(a1[i], b1[i], acc[0]);
+    acc[1] = fma(a2[i], b2[i], acc[1]);
+  }
+  block_partials<2>(acc, part);
+}
+
+// The same finish as a one-CTA kernel, after dot2_partial at the start of a solve.
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads) fin_kernel(const double* __restrict__ part, double* __restrict__ sc) {
+  if (sc[S_DONE] != 0.0) return;
+  finish<MODE>(part, sc);
+}
+
 __global__ void scal_init(double* sc) {
   sc[S_RHO_OLD] = 1.0; sc[S_ALPHA] = 1.0; sc[S_OMEGA] = 1.0; sc[S_FLAG] = 0.0; sc[S_BETA] = 0.0;
   sc[S_DONE] = 0.0; sc[S_ITER] = 0.0;
+  *reinterpret_cast<unsigned long long*>(sc + S_TICKET) = 0ull;
 }
 __global__ void iter_setup(double* sc, double target, double maxit) {
   sc[S_TARGET] = target;
@@ -463,13 +497,13 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
   const double bnorm = std::sqrt(h[S_BB]);
   const double target = rtol * (bnorm > 0.0 ? bnorm : 1.0);
   // One iteration's kernels; the loop's test runs on the device (at the end
-  // of the previous iteration, fin_kernel<kFinRrRho>), so kItersPerGraph
+  // of the previous iteration, in the last CTA of upd_xr_dot), so kItersPerGraph
   // iterations are captured once into a CUDA graph, kept on the grid for the
   // same buffers, and replayed until S_DONE.
   auto iteration = [&](cudaStream_t cs) {
     auto op_s = [&](const double* in, double* out) {
-      cudaError_t err = launch_spmv(g, val, 1.0, in, 0.0, out, transpose, cs, nb);
-      if (err == cudaSuccess && ws) err = launch_well_schur(g, *ws, 0, -1.0, in, out, nullptr, nullptr, cs);
+      cudaError_t err = launch_spmv(g, val, 1.0, in, 0.0, out, transpose, cs, nb, sc + S_DONE);
+      if (err == cudaSuccess && ws) err = launch_well_schur(g, *ws, 0, -1.0, in, out, nullptr, nullptr, cs, sc + S_DONE);
       return err;
     };
     cudaError_t err = cudaSuccess;
@@ -480,17 +514,14 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
     if (nb == 3) apply_dot<3><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, v, r0, sc, part);
     else if (nb == 2) apply_dot<2><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, v, r0, sc, part);
     else apply_dot<1><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, v, r0, sc, part);
-    fin_kernel<kFinAlpha><<<1, kRedThreads, 0, cs>>>(part, sc);
     upd_s<<<bn, 256, 0, cs>>>(n, r, v, sv, sc);
     // t = D^-1 A s, then omega = (t . s) / (t . t)
     if (err == cudaSuccess) err = op_s(sv, z);
     if (nb == 3) apply_dot2<3><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, t, sv, sc, part);
     else if (nb == 2) apply_dot2<2><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, t, sv, sc, part);
     else apply_dot2<1><<<kRedBlocks, kRedThreads, 0, cs>>>(n, dinv, z, t, sv, sc, part);
-    fin_kernel<kFinOmega><<<1, kRedThreads, 0, cs>>>(part, sc);
     // x += alpha p + omega s;  r = s - omega t;  then the loop's test, rho and beta
     upd_xr_dot<<<kRedBlocks, kRedThreads, 0, cs>>>(n, x, p, sv, r, t, r0, sc, part);
-    fin_kernel<kFinRrRho><<<1, kRedThreads, 0, cs>>>(part, sc);
     return err;
   };
   const void* key[8] = {val, work, x, ws ? ws->bs : nullptr, ws ? ws->cs : nullptr, ws ? ws->d : nullptr,

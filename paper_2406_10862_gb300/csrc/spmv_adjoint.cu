@@ -96,10 +96,11 @@ template <int NB>
 __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const int32_t* __restrict__ row_ptr,
                                                         const double* __restrict__ val, double alpha,
                                                         const double* __restrict__ x, double beta,
-                                                        double* __restrict__ y, int mode) {
+                                                        double* __restrict__ y, int mode,
+                                                        const double* __restrict__ skip) {
   constexpr int B2 = NB * NB;
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.N) return;
+  if (c >= P.N || (skip != nullptr && *skip != 0.0)) return;
   int ci, cj, ck;
   cell_ijk(P, c, ci, cj, ck);
   const bool has[7] = {ck > 0, cj > 0, ci > 0, true, ci + 1 < P.nx, cj + 1 < P.ny, ck + 1 < P.nz};
@@ -153,10 +154,11 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const
 template <int NB>
 __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_t_kernel(Params P, const double* __restrict__ val,
                                                                    double alpha, const double* __restrict__ x,
-                                                                   double beta, double* __restrict__ y, int mode) {
+                                                                   double beta, double* __restrict__ y, int mode,
+                                                                   const double* __restrict__ skip) {
   constexpr int B2 = NB * NB;
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.N) return;
+  if (c >= P.N || (skip != nullptr && *skip != 0.0)) return;
   int ci, cj, ck;
   cell_ijk(P, c, ci, cj, ck);
   const bool has[7] = {ck > 0, cj > 0, ci > 0, true, ci + 1 < P.nx, cj + 1 < P.ny, ck + 1 < P.nz};
@@ -234,9 +236,10 @@ __global__ void __launch_bounds__(kBulkRows) spmv_bulk_kernel(Params P, const in
                                                               long long nnzb, const double* __restrict__ val,
                                                               double alpha, const double* __restrict__ x,
                                                               double beta, double* __restrict__ y, int mode,
-                                                              int* __restrict__ status) {
+                                                              int* __restrict__ status, const double* __restrict__ skip) {
   constexpr int B2 = NB * NB;
   constexpr long long BB = 8 * B2;
+  if (skip != nullptr && *skip != 0.0) return;     // the same for every thread: before any barrier
   extern __shared__ __align__(128) unsigned char sbuf[];
   __shared__ __align__(8) unsigned long long bar;
   const long long r0 = (long long)blockIdx.x * kBulkRows;
@@ -478,7 +481,7 @@ cudaError_t launch_setup(ocp_grid* g, const double* d_lnk, double dx, double dy,
 }
 
 cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, const double* x, double beta,
-                        double* y, int transpose, cudaStream_t s, int nbs) {
+                        double* y, int transpose, cudaStream_t s, int nbs, const double* skip) {
   const long long N = g->prm.N;
   const int mode = (beta != 0.0) ? 2 : (alpha != 1.0 ? 1 : 0);
   const unsigned gblocks = (unsigned)((N + kSpmvThreads - 1) / kSpmvThreads);
@@ -489,16 +492,16 @@ cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, cons
   const bool bulk = ((uintptr_t)val & 15) == 0;
   const unsigned bblocks = (unsigned)((N + kBulkRows - 1) / kBulkRows);
   if (nb == 3) {
-    if (transpose) spmv_grid_t_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode);
-    else spmv_grid_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
+    if (transpose) spmv_grid_t_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode, skip);
+    else spmv_grid_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode, skip);
   } else if (nb == 2) {
-    if (transpose) spmv_grid_t_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode);
-    else if (bulk) spmv_bulk_kernel<2><<<bblocks, kBulkRows, bulk_smem_bytes<2>(), s>>>(g->prm, g->d_row_ptr, g->nnzb, val, alpha, x, beta, y, mode, g->d_status);
-    else spmv_grid_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
+    if (transpose) spmv_grid_t_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode, skip);
+    else if (bulk) spmv_bulk_kernel<2><<<bblocks, kBulkRows, bulk_smem_bytes<2>(), s>>>(g->prm, g->d_row_ptr, g->nnzb, val, alpha, x, beta, y, mode, g->d_status, skip);
+    else spmv_grid_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode, skip);
   } else {
-    if (transpose) spmv_grid_t_kernel<1><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode);
-    else if (bulk) spmv_bulk_kernel<1><<<bblocks, kBulkRows, bulk_smem_bytes<1>(), s>>>(g->prm, g->d_row_ptr, g->nnzb, val, alpha, x, beta, y, mode, g->d_status);
-    else spmv_grid_kernel<1><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode);
+    if (transpose) spmv_grid_t_kernel<1><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode, skip);
+    else if (bulk) spmv_bulk_kernel<1><<<bblocks, kBulkRows, bulk_smem_bytes<1>(), s>>>(g->prm, g->d_row_ptr, g->nnzb, val, alpha, x, beta, y, mode, g->d_status, skip);
+    else spmv_grid_kernel<1><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode, skip);
   }
   return cudaGetLastError();
 }

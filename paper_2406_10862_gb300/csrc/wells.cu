@@ -111,10 +111,11 @@ __global__ void __launch_bounds__(kWellThreads) schur_kernel(const Perf* __restr
                                                              const int32_t* __restrict__ first, int nwell,
                                                              WellSchur ws, double alpha,
                                                              const double* __restrict__ in, double* out,
-                                                             const double* __restrict__ bw, double* __restrict__ xw) {
+                                                             const double* __restrict__ bw, double* __restrict__ xw,
+                                                             const double* __restrict__ skip) {
   const int w = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (w >= nwell) return;
+  if (w >= nwell || (skip != nullptr && *skip != 0.0)) return;
   const int k0 = first[w], k1 = first[w + 1];
   double t = 0.0;
   if (MODE != 1) {
@@ -211,12 +212,13 @@ struct Guard {
 }  // namespace
 
 cudaError_t launch_well_schur(const ocp_grid* g, const WellSchur& ws, int mode, double alpha, const double* in,
-                              double* out, const double* bw, double* xw, cudaStream_t s) {
+                              double* out, const double* bw, double* xw, cudaStream_t s, const double* skip) {
   if (g->nwell == 0) return cudaSuccess;
   const unsigned nb = well_blocks(g->nwell);
   const bool three = g->prm.nb == 3;
 #define OCP_SCHUR(NBV, M) \
-  schur_kernel<NBV, M><<<nb, kWellThreads, 0, s>>>(g->d_perf, g->d_well_first, g->nwell, ws, alpha, in, out, bw, xw)
+  schur_kernel<NBV, M><<<nb, kWellThreads, 0, s>>>(g->d_perf, g->d_well_first, g->nwell, ws, alpha, in, out, bw, xw, \
+                                                    skip)
   if (mode == 0) { if (three) OCP_SCHUR(3, 0); else OCP_SCHUR(2, 0); }
   else if (mode == 1) { if (three) OCP_SCHUR(3, 1); else OCP_SCHUR(2, 1); }
   else { if (three) OCP_SCHUR(3, 2); else OCP_SCHUR(2, 2); }
