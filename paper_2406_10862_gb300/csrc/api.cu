@@ -278,7 +278,6 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = ocp::launch_setup(g, d_lnk, d->dx, d->dy, d->dz, d->kz_over_kx, 0);
   if (e == cudaSuccess) e = ocp::launch_perf_wi(g, d_lnk, 0);
-  if (e == cudaSuccess) e = ocp::configure_linearize_kernels();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(d_lnk);
   if (e != cudaSuccess) {

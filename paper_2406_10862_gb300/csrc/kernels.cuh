@@ -43,8 +43,6 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
                         cudaStream_t s, int nbs = 0);
 cudaError_t launch_tiles(int nb, const TileList* lists, const ModelArgs& single, const LaunchCfg& cfg,
                          int sms, cudaStream_t s);
-// Kernel attributes the linearisation needs on the current device (once per device, before any launch).
-cudaError_t configure_linearize_kernels();
 ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
                      const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
                      double* face_flux);

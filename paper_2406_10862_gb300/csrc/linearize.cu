@@ -40,53 +40,9 @@ constexpr int kInc = 49;    // shares handed over, 3 x (F 3 + dj 9)   49 .. 84
 // CellQ fields each block size reads (the two-phase path skips the gas and
 // dissolved-gas fields).
 template <int NB>
-__host__ __device__ constexpr bool q_used(int f) {
-  return NB == 3 || !(f == 2 || f == 4 || f == 9 || f == 10 || f == 11 || f == 18 || f >= 19);
-}
-template <int NB>
-__host__ __device__ constexpr int q_count() {
-  int n = 0;
-  for (int f = 0; f < kQ; ++f) n += q_used<NB>(f);
-  return n;
-}
-
-// face_kernel's per-thread prefetch: the 25 (13 with two phases) cell
-// quantities of the next face's neighbour go by cp.async into the thread's
-// own slots of a double buffer in shared memory, [2][fields][TPB], while the
-// thread computes the current face.  Each thread reads only what it copied
-// itself, so no CTA barrier is needed; cp.async.wait_group orders a thread's
-// reads after its copies.
-template <int NB, int TPB>
-__host__ __device__ constexpr int face_smem_bytes() { return 2 * q_count<NB>() * TPB * 8; }
-
-template <int NB, int TPB>
-__device__ __forceinline__ void prefetch_q(const double* __restrict__ scr, long long N, long long n, double* buf) {
-  int qi = 0;
-#pragma unroll
-  for (int f = 0; f < kQ; ++f) {
-    if (!q_used<NB>(f)) continue;
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(buf + qi * TPB + threadIdx.x);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(scr + f * N + n) : "memory");
-    ++qi;
-  }
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory"); }
-
-template <int NB, int TPB>
-__device__ __forceinline__ void read_q(const double* buf, CellQ& q) {
-  double* f = reinterpret_cast<double*>(&q);
-  int qi = 0;
-#pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    if (q_used<NB>(i)) {
-      f[i] = buf[qi * TPB + threadIdx.x];
-      ++qi;
-    } else {
-      f[i] = 0.0;
-    }
-  }
+__device__ __forceinline__ bool q_used(int f) {
+  if (NB == 3) return true;
+  return !(f == 2 || f == 4 || f == 9 || f == 10 || f == 11 || f == 18 || f >= 19);
 }
 
 template <int NB>
@@ -159,10 +115,9 @@ __device__ __forceinline__ void cell_body(const ModelArgs& M, const Table& T, lo
   }
 }
 
-template <int NB, int TPB>
-__device__ __forceinline__ void face_body(const ModelArgs& M, long long c, double* fbuf) {
+template <int NB>
+__device__ __forceinline__ void face_body(const ModelArgs& M, long long c) {
   constexpr int B2 = NB * NB;
-  constexpr int BUF = q_count<NB>() * TPB;      // doubles per buffer
   const Params& P = M.P;
   const long long N = P.N;
   double* __restrict__ scr = M.scr;
@@ -173,8 +128,6 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c, doubl
   const bool hm[3] = {i > 0, j > 0, k > 0};
   const bool hp[3] = {i + 1 < P.nx, j + 1 < P.ny, k + 1 < P.nz};
   const long long stride[3] = {1, P.nx, P.nxy};
-  if (hp[0]) prefetch_q<NB, TPB>(scr, N, c + 1, fbuf);   // the +x neighbour, while the own cell loads
-  cp_async_commit();
   CellQ a;
   load_q<NB>(scr, N, c, a);
   double r[NB], dg[NB][NB];
@@ -188,14 +141,6 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c, doubl
   int slot = (int)hm[0] + (int)hm[1] + (int)hm[2] + 1;   // first + block of this row
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
-    // the next face's neighbour goes in flight; this face's has landed
-    if (d < 2) {
-      if (hp[d + 1]) prefetch_q<NB, TPB>(scr, N, c + stride[d + 1], fbuf + ((d + 1) & 1) * BUF);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
     if (!hp[d]) {
       if (face_flux)
         for (int e = 0; e < NB; ++e) face_flux[(d * NB + e) * N + c] = 0.0;
@@ -203,7 +148,7 @@ __device__ __forceinline__ void face_body(const ModelArgs& M, long long c, doubl
     }
     const long long n = c + stride[d];
     CellQ b;
-    read_q<NB, TPB>(fbuf + (d & 1) * BUF, b);
+    load_q<NB>(scr, N, n, b);
     FaceOut<NB> o;
     const double T = M.trans[d * N + c];
     if (d == 2) face_terms<NB, true>(T, -P.grav_dz, a, b, o);
@@ -318,13 +263,12 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) cell_kernel(TileList L, ModelA
 
 template <int NB, int TPB>
 __global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) face_kernel(TileList L, ModelArgs single) {
-  extern __shared__ __align__(16) double fbuf[];
   for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
     int m;
     long long c0;
     const ModelArgs& M = tile_of<TPB>(L, single, t, m, c0);
     const long long c = c0 + threadIdx.x;
-    if (c < M.P.N) face_body<NB, TPB>(M, c, fbuf);
+    if (c < M.P.N) face_body<NB>(M, c);
   }
 }
 
@@ -342,28 +286,11 @@ __global__ void __launch_bounds__(TPB) assemble_kernel(TileList L, ModelArgs sin
 template <int NB, int TPB>
 void launch_stage(int stage, const TileList& L, const ModelArgs& single, int grid, cudaStream_t s) {
   if (stage == 0) cell_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
-  else if (stage == 1) face_kernel<NB, TPB><<<grid, TPB, face_smem_bytes<NB, TPB>(), s>>>(L, single);
+  else if (stage == 1) face_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
   else assemble_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
 }
 
 }  // namespace
-
-// The face kernel's prefetch buffers can exceed the default 48 KB of shared
-// memory; the attribute is set on the current device.
-cudaError_t configure_linearize_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(face_kernel<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       face_smem_bytes<3, 128>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(face_kernel<3, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             face_smem_bytes<3, 256>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(face_kernel<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             face_smem_bytes<2, 128>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(face_kernel<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             face_smem_bytes<2, 256>());
-  return e;
-}
 
 // Launches the three stages.  `lists[0]` / `lists[1]` are the tile lists for
 // 128 / 256 cells per tile; cfg picks, per stage, the tile size and the grid
