@@ -137,8 +137,8 @@ ocp_status ocp_linearize(ocp_grid* grid, const double* u_new, const int8_t* flag
 /* ocp_linearize without any device allocation behind it.  The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc
  * when they linearise -- code whose device memory is owned by a host
- * application or framework, a loop under a fixed memory budget, or work that
- * will be captured into a CUDA graph, where allocation is not allowed.
+ * application or framework with its own allocator, or a loop under a fixed
+ * memory budget that may not grow.
  * Same arguments, outputs and errors as ocp_linearize, but its per-cell
  * scratch is a 32 MiB array owned by the library (held on every GPU that
  * loads it until the process exits) instead of the grid's buffer, so it

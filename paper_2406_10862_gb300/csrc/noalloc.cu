@@ -3,11 +3,10 @@
 //
 // Who needs it: code that must not allocate device memory at the moment it
 // linearises -- a caller whose memory is owned by a host application or an
-// embedding framework with its own allocator, a real-time loop under a fixed
-// memory budget, or a code path that will later be captured into a CUDA graph
-// (allocation calls are not allowed while a stream is being captured).  Such a
-// caller still passes its inputs and outputs; this entry point itself calls no
-// cudaMalloc, cudaFree or any allocating routine.
+// embedding framework with its own allocator, or a real-time loop under a
+// fixed memory budget that may not grow.  Such a caller still passes its
+// inputs and outputs; this entry point itself calls no cudaMalloc, cudaFree
+// or any allocating routine.
 //
 // The array holds kStaticScratchDoubles doubles (32 MiB).  Every GPU that
 // loads the library holds it until the process exits.  The scratch needs 100

@@ -1,8 +1,8 @@
 """ocp_linearize_noalloc against ocp_linearize.
 
 The no-allocation entry point serves callers that cannot call cudaMalloc
-when they linearise (memory owned by a host framework, a fixed budget, work
-captured into a CUDA graph).  It must give the same residual, Jacobian and
+when they linearise (memory owned by a host framework with its own allocator,
+a fixed memory budget).  It must give the same residual, Jacobian and
 face fluxes as the ordinary entry point -- within the tolerances of every
 other parity test -- on consecutive calls that reuse its shared scratch, and
 reject grids larger than its fixed array.  This file is collected last so a
