@@ -59,7 +59,7 @@ typedef enum {
   OCP_ERR_OOM = 3,          /* device allocation failed */
   OCP_ERR_NONFINITE = 4,    /* a kernel met a NaN/Inf input or produced one */
   OCP_ERR_TIMEOUT = 5,      /* a bounded wait expired */
-  OCP_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+  OCP_ERR_UNSUPPORTED = 6   /* valid request the library does not implement */
 } ocp_status;
 
 /* A well controlled by bottom-hole pressure (AllWells, Sec. 3.2.4).  Each
