@@ -49,6 +49,15 @@ MUTATIONS = [
     ("linearize.py", "return D(e, e[:, None] * a.g, ae, ae[:, None] * a.gm)",
      "return D(e, a.g, ae, ae[:, None] * a.gm)"),                              # d exp(x) = exp(x) dx
     ("dual.py", "dv = e * self.v ** (e - 1.0)", "dv = self.v ** (e - 1.0)"),   # power rule factor
+    # the last entries name the pin that must catch them
+    ("linearize.py", "r_o = 0.14 * np.sqrt(spec.dx ** 2 + spec.dy ** 2)",
+     "r_o = 0.20 * np.sqrt(spec.dx ** 2 + spec.dy ** 2)", "pin_peaceman"),    # Peaceman radius
+    ("blackoil.py", "(1.0 - spec.cmu_under * dp)", "(1.0 + spec.cmu_under * dp)",
+     "pin_undersaturated"),                                                    # viscosibility sign
+    ("blackoil.py", "(1.0 + spec.co_under * dp)", "(1.0 + 2.0 * spec.co_under * dp)",
+     "pin_undersaturated"),                                                    # compressibility
+    ("blackoil.py", "pb = interp_on(cols[\"Rs\"], knots, kr, x)",
+     "pb = interp_on(cols[\"Rs\"], knots, kr, x) + 1.0", "pin_undersaturated"),   # bubble point off
 ]
 
 
@@ -56,7 +65,7 @@ def load_oracle(tmp_path, tag, mutation=None):
     dst = tmp_path / ("oracle_" + tag)
     shutil.copytree(os.path.join(ROOT, "oracle"), dst)
     if mutation is not None:
-        fname, old, new = mutation
+        fname, old, new = mutation[:3]
         f = dst / fname
         src = f.read_text()
         assert src.count(old) == 1, (fname, old)
@@ -255,9 +264,65 @@ def pin_complex_step(lin, newton, bo):
     return True
 
 
+def pin_undersaturated(lin, newton, bo):
+    """Continuity at the bubble point and the closed forms above it, with
+    c_mu != 0 (compact form of the pins in test_oracle_pins.py)."""
+    g, _ = W.tiny(1, 1, 1, co_under=1e-5, cmu_under=2e-5)
+    knots, cols = bo.table_columns(g)
+    D = bo.D
+
+    def props(p, x, flag):
+        n = len(p)
+        pr = bo.cell_properties(g, D.seed(p, 2, 0), D.const(0.3, n, 2), D.seed(x, 2, 1),
+                                np.full(n, flag, dtype=np.int8), np.full(n, 0.2))
+        return pr
+
+    p = np.concatenate([knots[:-1], 0.5 * (knots[:-1] + knots[1:])])
+    un, sa = props(p, 0.3 * p, 1), props(p, np.zeros_like(p), 0)
+    ok = all(np.allclose(un[k].v, sa[k].v, rtol=1e-13, atol=0) for k in ("b_o", "imu_o", "rho_o", "lam_o"))
+    k = 7
+    dp = np.array([0.0, 400.0, 1750.0])
+    pr = props(knots[k] + dp, np.full(3, cols["Rs"][k]), 1)
+    ok = ok and np.allclose(pr["b_o"].v, cols["b_o"][k] * (1.0 + 1e-5 * dp), rtol=1e-14)
+    ok = ok and np.allclose(pr["imu_o"].v, cols["imu_o"][k] * (1.0 - 2e-5 * dp), rtol=1e-14)
+    return bool(ok)
+
+
+def pin_peaceman(lin, newton, bo):
+    """The pressure around a producer in a homogeneous 2-D grid with a
+    fixed-pressure outer ring follows p_bh + q/(2 pi C k h lambda) ln(r/r_w)
+    (compact form of the pin in test_oracle_pins.py)."""
+    import scipy.sparse.linalg as spla
+    from oracle.spmv import bsr_to_scipy
+    n, m, dx = 31, 20, 100.0
+    g = W.make_grid(n, n, 1, np.full(n * n, math.log(100.0)), np.full(n * n, 0.2), [], nphase=2,
+                    dx=dx, dy=dx, dz=20.0, tab_Bo=np.full(m, 1.25), tab_muo=np.full(m, 0.8), cw=0.0, cr=0.0,
+                    pcow_max=0.0)
+    c = n // 2
+    g.wells = [W.Well(kind=0, phase=0, p_bh=2000.0, cells=np.array([g.cell(c, c, 0)]))]
+    N = g.N
+    u = np.zeros((2, N))
+    u[0], u[1] = 3000.0, g.swc
+    flag = np.zeros(N, dtype=np.int8)
+    o = lin.linearize(g, u, flag, u, flag, 1.0)
+    A = bsr_to_scipy(o["row_ptr"], o["col_idx"], o["val"]).tocsr()
+    i, j = np.arange(N) % n, np.arange(N) // n
+    free = np.repeat(~((i == 0) | (j == 0) | (i == n - 1) | (j == n - 1)), 2)
+    du = np.zeros(2 * N)
+    du[free] = spla.spsolve(A[free][:, free].tocsc(), -o["R"].ravel()[free])
+    u1 = u + du.reshape(N, 2).T
+    q = -lin.linearize(g, u1, flag, u, flag, 1.0)["well_rate"][0, 1]
+    a = q / (2.0 * math.pi * 0.001127 * 100.0 * 20.0 * (1.0 / 1.25 / 0.8))
+    ok = True
+    for di, dj in [(3, 0), (4, 0), (3, 3)]:
+        r = math.hypot(di, dj) * dx
+        ok = ok and abs((u1[0, g.cell(c + di, c + dj, 0)] - 2000.0) / (a * math.log(r / 0.25)) - 1.0) < 4e-3
+    return bool(ok)
+
+
 PINS = [pin_mass_balance, pin_fd, pin_complex_step, pin_hydrostatic, pin_compressible_column, pin_capillary_direction,
         pin_tables, pin_laplacian, pin_surface_density_and_stone,
-        pin_buckley_leverett]
+        pin_buckley_leverett, pin_undersaturated, pin_peaceman]
 
 
 def test_unmodified_oracle_passes_compact_pins(tmp_path):
@@ -280,3 +345,10 @@ def test_planted_mistake_is_caught(tmp_path, k):
             failed.append(pin.__name__)
             break
     assert failed, "mutation %r passed every pin" % (MUTATIONS[k][1],)
+    if len(MUTATIONS[k]) > 3:
+        named = [p for p in PINS if p.__name__ == MUTATIONS[k][3]][0]
+        try:
+            ok = named(lin, newton, bo)
+        except Exception:
+            ok = False
+        assert not ok, "mutation %r is not caught by %s" % (MUTATIONS[k][1], MUTATIONS[k][3])

@@ -10,6 +10,7 @@ import math
 
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spla
 
 from oracle import blackoil as bo
 from oracle.dual import D
@@ -424,3 +425,130 @@ def test_adjoint_dot_product_and_parameter_gradients():
             sm.u_old[vv, c] -= h
             fd = (f(g, sp) - f(g, sm)) / (2 * h)
             assert fd == pytest.approx(o["g_uold"][vv, c], rel=1e-6)
+
+
+# ------------------------------------------------- undersaturated oil (R4)
+def _oil_props(g, p, x, flag, sw=0.3):
+    """Oil properties of cells at (p, S_w, X) as dual numbers in (p, X)."""
+    n = len(p)
+    P = D.seed(np.asarray(p, dtype=np.float64), 2, 0)
+    X = D.seed(np.asarray(x, dtype=np.float64), 2, 1)
+    pr = bo.cell_properties(g, P, D.const(sw, n, 2), X, np.full(n, flag, dtype=np.int8), np.full(n, 0.2))
+    return pr, bo.masses(g, pr)
+
+
+def test_undersaturated_oil_is_continuous_at_the_bubble_point():
+    """At p = p_b(R_s) the undersaturated oil is the saturated oil without
+    free gas: the same b_o, 1/mu_o, R_s, density, mobility and component
+    amounts on either side of the phase switch (Sec. 2.1: the black-oil
+    closure is explicit in the primary variables; reading R4), with nonzero
+    oil compressibility and viscosibility so that a wrong bubble point, a
+    wrong piece of the inverse table or a misplaced p - p_b shows."""
+    g, _ = W.tiny(1, 1, 1, co_under=1e-5, cmu_under=2e-5)
+    knots, cols = bo.table_columns(g)
+    # knots (right-hand piece), interior points of pieces, both table ends
+    p = np.concatenate([knots[:-1], 0.5 * (knots[:-1] + knots[1:]), [knots[-1], 417.25, 6123.5]])
+    rs = 0.3 * p                                    # R_s,sat(p) of the exactly linear table
+    un, mu = _oil_props(g, p, rs, 1)
+    sa, ms = _oil_props(g, p, np.zeros_like(p), 0)
+    for key in ("b_o", "imu_o", "Rs", "rho_o", "lam_o", "kr_o", "S_o"):
+        np.testing.assert_allclose(un[key].v, sa[key].v, rtol=1e-13, atol=0, err_msg=key)
+    for e in range(3):
+        np.testing.assert_allclose(mu[e].v, ms[e].v, rtol=1e-13, atol=0, err_msg="m[%d]" % e)
+    np.testing.assert_array_equal(un["S_g"].v, 0.0)
+    np.testing.assert_array_equal(un["S_g"].g, 0.0)
+
+
+@pytest.mark.parametrize("co,cmu", [(1e-5, 0.0), (1e-5, 2e-5), (3e-5, -1e-5)])
+def test_undersaturated_oil_compressibility_closed_forms(co, cmu):
+    """With the bubble point on a knot p_k (X = R_s at the knot, so p_b = p_k
+    exactly) the undersaturated oil follows the closed forms of a constant
+    compressibility c_o and viscosibility c_mu above it (reading R4):
+      b_o = b_k (1 + c_o dp),  d ln b_o / dp = c_o / (1 + c_o dp),
+      1/mu_o = (1/mu)_k (1 - c_mu dp), d ln(1/mu_o)/dp = -c_mu / (1 - c_mu dp),
+    dp = p - p_k; and with respect to X, through dp_b/dX = 1/0.3 (the slope
+    of the inverse of R_s = 0.3 p), the chain rule of the same forms on the
+    table piece to the right of the knot."""
+    g, _ = W.tiny(1, 1, 1, co_under=co, cmu_under=cmu)
+    knots, cols = bo.table_columns(g)
+    b, imu = cols["b_o"], cols["imu_o"]
+    for k in (0, 7, 13):
+        dp = np.array([0.0, 25.0, 400.0, 1750.0])
+        p = knots[k] + dp
+        x = np.full(len(p), cols["Rs"][k])
+        pr, m = _oil_props(g, p, x, 1)
+        sb = (b[k + 1] - b[k]) / (knots[k + 1] - knots[k])
+        si = (imu[k + 1] - imu[k]) / (knots[k + 1] - knots[k])
+        np.testing.assert_allclose(pr["b_o"].v, b[k] * (1.0 + co * dp), rtol=1e-14)
+        np.testing.assert_allclose(pr["b_o"].g[:, 0] / pr["b_o"].v, co / (1.0 + co * dp), rtol=1e-12, atol=0)
+        np.testing.assert_allclose(pr["imu_o"].v, imu[k] * (1.0 - cmu * dp), rtol=1e-14)
+        np.testing.assert_allclose(pr["imu_o"].g[:, 0] / pr["imu_o"].v, -cmu / (1.0 - cmu * dp),
+                                   rtol=1e-12, atol=1e-300)
+        dpb = 1.0 / 0.3
+        np.testing.assert_allclose(pr["b_o"].g[:, 1], dpb * (sb * (1.0 + co * dp) - co * b[k]), rtol=1e-12,
+                                   atol=1e-18)
+        np.testing.assert_allclose(pr["imu_o"].g[:, 1], dpb * (si * (1.0 - cmu * dp) + cmu * imu[k]),
+                                   rtol=1e-12, atol=1e-18)
+        # all gas dissolved: R_s is the unknown, no free gas, m_g = R_s m_o
+        np.testing.assert_array_equal(pr["Rs"].v, x)
+        np.testing.assert_array_equal(pr["Rs"].g, np.tile([0.0, 1.0], (len(p), 1)))
+        np.testing.assert_allclose(m[2].v, x * m[1].v, rtol=1e-15)
+
+
+# ------------------------------------------------------- Peaceman (R10)
+def _radial_flow(nx, ny, dx, dy, k=100.0, h=20.0, p_e=3000.0, p_bh=2000.0):
+    """Steady, incompressible, single-phase flow to one producer in the
+    centre of a homogeneous 2-D grid whose outer ring of cells is held at
+    p_e: the oracle's residual is affine in p here (flat tables, no rock or
+    water compressibility, immobile water at S_wc, no gravity in one
+    layer), so one Newton step from the uniform state with the ring's
+    unknowns fixed is the exact discrete solution.  Returns the grid, the
+    pressures, the oil production rate and q / (2 pi C k h lambda_o)."""
+    m = 20
+    g = W.make_grid(nx, ny, 1, np.full(nx * ny, math.log(k)), np.full(nx * ny, 0.2), [], nphase=2,
+                    dx=dx, dy=dy, dz=h, tab_Bo=np.full(m, 1.25), tab_muo=np.full(m, 0.8), cw=0.0, cr=0.0,
+                    pcow_max=0.0)
+    cx, cy = nx // 2, ny // 2
+    g.wells = [W.Well(kind=0, phase=0, p_bh=p_bh, cells=np.array([g.cell(cx, cy, 0)]))]
+    N = g.N
+    u = np.zeros((2, N))
+    u[0] = p_e
+    u[1] = g.swc
+    flag = np.zeros(N, dtype=np.int8)
+    o = linearize(g, u, flag, u, flag, 1.0)
+    A = bsr_to_scipy(o["row_ptr"], o["col_idx"], o["val"]).tocsr()
+    i, j = np.arange(N) % nx, np.arange(N) // nx
+    ring = (i == 0) | (j == 0) | (i == nx - 1) | (j == ny - 1)
+    free = np.repeat(~ring, 2)
+    du = np.zeros(2 * N)
+    du[free] = spla.spsolve(A[free][:, free].tocsc(), -o["R"].ravel()[free])
+    u1 = u + du.reshape(N, 2).T
+    o1 = linearize(g, u1, flag, u, flag, 1.0)
+    assert np.max(np.abs(o1["R"][~ring])) < 1e-9 * np.max(np.abs(o1["R_mag"]))   # solved
+    assert np.all(du[1::2] == 0.0)                                               # water stays put
+    q = -o1["well_rate"][0, 1]
+    lam_o = g.kro_cw / 1.25 / 0.8
+    return g, u1[0], q, q / (2.0 * math.pi * bo.C_DARCY * k * h * lam_o), (cx, cy)
+
+
+@pytest.mark.parametrize("nx,ny,dx,dy,tol", [(41, 41, 100.0, 100.0, 3e-3), (41, 61, 100.0, 60.0, 1e-2)])
+def test_peaceman_well_reproduces_radial_flow(nx, ny, dx, dy, tol):
+    """Peaceman's equivalent radius: with WI = 2 pi C k h / ln(r_o / r_w) and
+    r_o = 0.14 sqrt(dx^2 + dy^2) (reading R10), the discrete pressure field
+    around a producing well matches the continuous radial solution
+    p(r) = p_bh + q / (2 pi C k h lambda) ln(r / r_w) away from the well
+    block, because r_o is the radius at which the five-point scheme's
+    well-block pressure sits on that solution (Peaceman's derivation; for
+    square cells the lattice Green's function gives r_o = 0.1985 dx, and
+    0.14 sqrt(2) dx = 0.1980 dx).  Differences between two far-field cells
+    follow the same log law."""
+    g, p, q, a, (cx, cy) = _radial_flow(nx, ny, dx, dy)
+    assert q > 0.0
+    rw = g.wells[0].rw
+    for di, dj in [(3, 0), (4, 0), (6, 0), (3, 3), (4, 4), (5, 3), (-3, 0), (0, -4)]:
+        r = math.hypot(di * dx, dj * dy)
+        got = p[g.cell(cx + di, cy + dj, 0)] - 2000.0
+        assert got == pytest.approx(a * math.log(r / rw), rel=tol), (di, dj)
+    r1, r2 = 3 * dx, 6 * dx
+    diff = p[g.cell(cx + 6, cy, 0)] - p[g.cell(cx + 3, cy, 0)]
+    assert diff == pytest.approx(a * math.log(r2 / r1), rel=5 * tol)
