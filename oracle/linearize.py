@@ -115,7 +115,8 @@ def bsr_pattern(spec):
 
 
 # ----------------------------------------------------------------- linearise
-def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None, p_bh=None, controls=None):
+def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None, p_bh=None, controls=None,
+              up_flip=None):
     """Residual and Jacobian of one backward-Euler step.
 
     mode="unew": derivatives with respect to the new state only (the Jacobian).
@@ -133,6 +134,16 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
     p_bh.  The extra outputs are ``well_res`` (nwell), ``well_B`` (nperf, nb)
     = dR_cell/dp_bh, ``well_C`` (nperf, nb) = dR_w/du_cell, ``well_D`` (nwell)
     = dR_w/dp_bh, each with its magnitude scale, perforations in well order.
+
+    ``up_flip`` maps (direction, phase letter) to a boolean array over that
+    direction's faces (``face_pairs`` order): where True, the upwind cell of
+    that phase is the other one.  It exists for faces whose potential
+    difference is zero to within rounding (a hydrostatic state): there the
+    sign, and with it the side that reading X10 picks, is decided by rounding
+    alone, the flux vanishes either way, and both one-sided derivatives are
+    correct results.  Default: no face flipped.  ``face_dphi`` and
+    ``face_dphi_mag`` hold every face's potential difference and its
+    magnitude scale, the latter bounding how far rounding can move it.
     """
     nx, ny, nz = dims(spec)
     N = nx * ny * nz
@@ -198,6 +209,7 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
     face_flux = np.zeros((3, nb, N), dtype=cdt)
     face_flux_mag = np.zeros((3, nb, N))
     face_dphi = {}
+    face_dphi_mag = {}
     for d in range(3):
         fi, fj = face_pairs(spec, d)
         if len(fi) == 0:
@@ -212,10 +224,13 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
             gamma = (Pi["rho_" + a] + Pj["rho_" + a]) * (0.5 * GRAV)
             dphi = (Pi["p_" + a] - Pj["p_" + a]) - gamma * dz_ij
             up_i = dphi.v >= 0.0
+            if up_flip is not None and (d, a) in up_flip:
+                up_i = up_i ^ np.asarray(up_flip[(d, a)], dtype=bool)
             lam_up = where(up_i, Pi["lam_" + a], Pj["lam_" + a])
             F[a] = T * lam_up * dphi
             F["up_" + a] = up_i
             face_dphi[(d, a)] = dphi.v
+            face_dphi_mag[(d, a)] = dphi.m
         comp = [F["w"], F["o"]]
         if nb == 3:
             rs_up = where(F["up_o"], Pi["Rs"], Pj["Rs"])
@@ -334,7 +349,7 @@ def linearize(spec, u_new, flag_new, u_old, flag_old, dt, mode="unew", lam=None,
         "val": val, "val_mag": valm, "acc": np.stack([a.v for a in acc], axis=1),
         "well_q": well_q, "well_rate": well_rate, "well_grad": well_grad,
         "face_flux": face_flux, "face_flux_mag": face_flux_mag,
-        "face_dphi": face_dphi,
+        "face_dphi": face_dphi, "face_dphi_mag": face_dphi_mag,
     }
     if unknown_bhp:
         cat = lambda parts: np.concatenate(parts) if parts else np.zeros((0, nb))

@@ -552,3 +552,40 @@ def test_peaceman_well_reproduces_radial_flow(nx, ny, dx, dy, tol):
     r1, r2 = 3 * dx, 6 * dx
     diff = p[g.cell(cx + 6, cy, 0)] - p[g.cell(cx + 3, cy, 0)]
     assert diff == pytest.approx(a * math.log(r2 / r1), rel=5 * tol)
+
+
+# ----------------------------------------------------------- X10 at a tie
+def test_upwind_flip_at_a_tie_changes_no_flux():
+    """At a face whose potential difference is zero the flux vanishes
+    whichever side is upwind (eq. 2: F = T lambda_up dphi), so flipping the
+    upwind choice there (the oracle's ``up_flip``) leaves the residual and
+    the face fluxes unchanged while the Jacobian's face blocks move to the
+    other cell's mobility; on an untied face the flip changes the flux."""
+    n = 20
+    g, _ = W.tiny(3, 2, 6, seed=23, wells=False, **flat_fluid(cw=1e-4))
+    z = g.top_depth + (np.arange(g.N) // (g.nx * g.ny) + 0.5) * g.dz
+    # rho_w = rho_wsc b_w(p) is affine in p here, so the column at rest solves
+    # p_k+1 - p_k = G (rho_k + rho_k+1) / 2 in closed form, G = g dz
+    G, r0, c = bo.GRAV * g.dz, g.rho_wsc * g.bw_ref, g.cw
+    a = 0.5 * G * r0 * c
+    p = np.zeros(g.nz)
+    p[0] = 3000.0
+    for k in range(g.nz - 1):
+        p[k + 1] = (p[k] * (1.0 + a) + G * r0 * (1.0 - c * g.p_ref)) / (1.0 - a)
+    u = np.zeros((3, g.N))
+    u[0] = p[np.arange(g.N) // (g.nx * g.ny)]
+    u[1], u[2] = 0.5, 0.0
+    f = np.zeros(g.N, dtype=np.int8)
+    o = linearize(g, u, f, u, f, 1.0)
+    dphi, mag = o["face_dphi"][(2, "w")], o["face_dphi_mag"][(2, "w")]
+    assert np.all(np.abs(dphi) <= 64 * np.finfo(float).eps * mag)
+    flip = {(2, "w"): np.ones(len(dphi), dtype=bool)}
+    of = linearize(g, u, f, u, f, 1.0, up_flip=flip)
+    np.testing.assert_allclose(of["R"], o["R"], rtol=0, atol=1e-12 * o["R_mag"].max())
+    np.testing.assert_allclose(of["face_flux"], o["face_flux"], rtol=0, atol=1e-12 * o["face_flux_mag"].max())
+    assert np.max(np.abs(of["val"] - o["val"]) / (o["val_mag"] + 1e-300)) > 1e-6
+    # an untied face: the flip changes the flux
+    g2, s2 = W.tiny(3, 2, 2, seed=4)
+    o2 = lin(g2, s2)
+    f2 = lin(g2, s2, up_flip={(0, "o"): np.ones(len(face_pairs(g2, 0)[0]), dtype=bool)})
+    assert np.max(np.abs(f2["face_flux"][0, 1] - o2["face_flux"][0, 1])) > 1e-3 * np.max(np.abs(o2["face_flux"][0, 1]))
