@@ -140,13 +140,16 @@ ocp_status ocp_linearize(ocp_grid* grid, const double* u_new, const int8_t* flag
  * application or framework with its own allocator, or a loop under a fixed
  * memory budget that may not grow.
  * Same arguments, outputs and errors as ocp_linearize, but its per-cell
- * scratch is a 32 MiB array owned by the library (held on every GPU that
- * loads it until the process exits) instead of the grid's buffer, so it
- * accepts grids of at most 41 943 cells and returns OCP_ERR_INVALID_ARG for
- * larger ones.  It calls no cudaMalloc, cudaFree or other allocating routine.
- * The first call on each device looks up the array's device address; make
- * that first call before any stream capture.  All calls share the array:
- * calls that overlap on the GPU race and must not be made. */
+ * scratch is a 32 MiB array owned by the library instead of the grid's
+ * buffer, so it accepts grids of at most 41 943 cells and returns
+ * OCP_ERR_INVALID_ARG for larger ones.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine, and triggers no lazy module load: the array is
+ * reserved on a device, and the kernels loaded there, by the first
+ * ocp_grid_create on that device (which allocates anyway); the array stays
+ * reserved until the process exits, and the grid keeps its device address.
+ * A device reset invalidates the grid and that address with it.  All calls
+ * share the array and leave its contents behind (nothing in it needs to
+ * start at zero): calls that overlap on the GPU race and must not be made. */
 ocp_status ocp_linearize_noalloc(ocp_grid* grid, const double* u_new, const int8_t* flag_new,
                                  const double* u_old, const int8_t* flag_old, double dt,
                                  double* residual, double* bsr_val, double* face_flux, void* cuda_stream);
@@ -208,11 +211,22 @@ typedef struct {
 } ocp_batch_io;
 
 /* Launch shape of the three stages (0 cell, 1 face, 2 assembly): cells per
- * tile (128 or 256; one thread per cell) and CTAs per SM of a persistent
- * launch (1..64), or 0 for one CTA per tile.  Results do not depend on it. */
+ * tile (32, 64, 128 or 256; one thread per cell) and CTAs per SM of a persistent
+ * launch (1..64), or 0 for one CTA per tile.
+ * ordered = 0: three launches, one per stage.  ordered = 1: the cell stage as
+ * above, then one persistent launch in which each CTA claims the face stage
+ * of one tile after another from a device counter, in tile order, and
+ * assembles the tile's rows once the tiles holding their - neighbours have
+ * finished their faces (tile size cells_per_tile[1]; ctas_per_sm[1] CTAs per
+ * SM, 0: as many as fit).  ordered = 2: one persistent launch of both the
+ * cell and the face stages, each tile's cell stage claimed ahead of the face
+ * stages that need it.  The waits on other tiles are bounded: one that
+ * expires makes ocp_get_status return OCP_ERR_TIMEOUT.
+ * Results do not depend on the shape, bit for bit. */
 typedef struct {
   int cells_per_tile[3];
   int ctas_per_sm[3];
+  int ordered;
 } ocp_launch_shape;
 
 /* Groups n >= 1 grids (same device, same number of phases; each grid may
@@ -235,9 +249,11 @@ ocp_status ocp_batch_linearize(ocp_batch* batch, double dt, void* cuda_stream);
  * a private stream) into a CUDA graph that is replayed on cuda_stream. */
 ocp_status ocp_batch_graph_launch(ocp_batch* batch, double dt, void* cuda_stream);
 
-/* Autotuner: times every stage with 2 tile sizes x 6 grid sizes (median of
- * reps after a warm-up) and keeps the fastest per stage; returns it in *best
- * (may be NULL).  Synchronises the stream many times. */
+/* Autotuner: times every stage with 4 tile sizes x 6 grid sizes (median of
+ * reps after a warm-up) and keeps the fastest per stage, then times the whole
+ * pass so found against the ordered launches (modes 1 and 2, 4 tile sizes,
+ * 4 grid sizes) and keeps the fastest; returns it in *best (may be NULL).
+ * Synchronises the stream many times. */
 ocp_status ocp_batch_tune(ocp_batch* batch, double dt, int reps, ocp_launch_shape* best, void* cuda_stream);
 ocp_status ocp_batch_set_shape(ocp_batch* batch, const ocp_launch_shape* shape);
 ocp_status ocp_batch_get_shape(const ocp_batch* batch, ocp_launch_shape* shape);
@@ -246,8 +262,13 @@ ocp_status ocp_batch_get_shape(const ocp_batch* batch, ocp_launch_shape* shape);
 ocp_status ocp_batch_get_status(ocp_batch* batch, void* cuda_stream);
 
 /* Launch shape of ocp_linearize on one grid (for example one found by
- * ocp_batch_tune on a batch of that grid alone). */
+ * ocp_batch_tune on a batch of that grid alone).  A new grid starts with one
+ * CTA per tile and the largest tiles (128 cells for the cell and face stages,
+ * 256 for assembly) that still give every SM two CTAs, halving down to 32
+ * cells for small grids. */
 ocp_status ocp_grid_set_shape(ocp_grid* grid, const ocp_launch_shape* shape);
+/* The launch shape ocp_linearize currently uses on the grid. */
+ocp_status ocp_grid_get_shape(const ocp_grid* grid, ocp_launch_shape* shape);
 
 /* ---------------------------------------------------------------- Newton step
  * The rest of the FIM nonlinear iteration of Sec. 3.2.5 -- the linear solve

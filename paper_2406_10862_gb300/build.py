@@ -37,7 +37,7 @@ def _sources():
 def _fingerprint(extra):
     h = hashlib.sha256()
     files = _sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
-    files.append(os.path.join(INCLUDE, "ocp.h"))
+    files += sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
     for f in files:
         h.update(f.encode())
         with open(f, "rb") as fh:

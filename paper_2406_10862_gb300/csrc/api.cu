@@ -56,6 +56,7 @@ void free_grid(ocp_grid* g) {
   cudaFree(g->d_well_first);
   cudaFree(g->d_status);
   cudaFree(g->d_scratch);
+  cudaFree(g->d_sync);
   cudaFree(g->d_pn);
   if (g->solve_exec) cudaGraphExecDestroy(g->solve_exec);
   if (g->solve_cap) cudaStreamDestroy(g->solve_cap);
@@ -235,13 +236,6 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   P.bw_p_imu = (d->bw_ref * d->cw) * P.imu_w;
   P.vol_rb = d->dx * d->dy * d->dz / ocp::kRbFt3;
 
-  // default launch shape: 128-cell tiles for the register-heavy cell and
-  // face stages, 256 for assembly, one CTA per tile (ocp_grid_set_shape and
-  // the batch autotuner can change it)
-  for (int s = 0; s < 3; ++s) {
-    g->cfg.tpb[s] = s < 2 ? 128 : 256;
-    g->cfg.ctas_per_sm[s] = 0;
-  }
   g->sms = 0;
   g->dx = d->dx;
   g->dy = d->dy;
@@ -264,9 +258,13 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   OCP_ALLOC(g->d_well_first, sizeof(int32_t) * well_first.size());
   OCP_ALLOC(g->d_status, sizeof(int));
   OCP_ALLOC(g->d_scratch, sizeof(double) * g->scratch_doubles);
+  OCP_ALLOC(g->d_sync, sizeof(unsigned) * (1 + 2 * ((N + 31) / 32)));
   OCP_ALLOC(d_lnk, sizeof(double) * N);
 #undef OCP_ALLOC
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, device);
+  // default launch shape (ocp_grid_set_shape and the batch autotuner can
+  // change it): one CTA per tile, tiles as large as the grid's size allows
+  g->cfg = ocp::default_cfg(N, g->sms);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_table, &T, sizeof(T), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_phi, d->phi, sizeof(double) * N, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_lnk, d->lnk, sizeof(double) * N, cudaMemcpyHostToDevice);
@@ -278,6 +276,10 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = ocp::launch_setup(g, d_lnk, d->dx, d->dy, d->dz, d->kz_over_kx, 0);
   if (e == cudaSuccess) e = ocp::launch_perf_wi(g, d_lnk, 0);
+  // the no-allocation entry point's array and kernels, loaded now (this call
+  // allocates anyway) so that that entry point never triggers a lazy load
+  if (e == cudaSuccess) e = ocp::static_scratch_address(&g->d_static_scratch);
+  if (e == cudaSuccess) e = ocp::preload_linearize(nb);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(d_lnk);
   if (e != cudaSuccess) {

@@ -21,8 +21,14 @@ struct ocp_batch {
   std::vector<ocp_grid*> grids;
   ocp::ModelArgs* h_models = nullptr;   // pinned staging of the argument table
   ocp::ModelArgs* d_models = nullptr;
-  int2* d_tiles[2] = {nullptr, nullptr};
-  int ntiles[2] = {0, 0};
+  int2* d_tiles[ocp::kNumTileSizes] = {};
+  int ntiles[ocp::kNumTileSizes] = {};
+  // ordered launch: models largest first, tiles of the models before each
+  // (per tile size), and the item counter plus cell and face flags
+  int* d_order = nullptr;
+  long long* d_tile_start[ocp::kNumTileSizes] = {};
+  unsigned* d_sync = nullptr;
+  long long nsync_tiles = 0;             // flags per stage (tiles of 32 cells)
   ocp::LaunchCfg cfg;
   bool io_set = false;
   bool dirty = true;                     // host table newer than the device one
@@ -53,13 +59,17 @@ void free_batch(ocp_batch* b) {
   if (b->cap) cudaStreamDestroy(b->cap);
   cudaFreeHost(b->h_models);
   cudaFree(b->d_models);
-  cudaFree(b->d_tiles[0]);
-  cudaFree(b->d_tiles[1]);
+  for (int t = 0; t < ocp::kNumTileSizes; ++t) {
+    cudaFree(b->d_tiles[t]);
+    cudaFree(b->d_tile_start[t]);
+  }
+  cudaFree(b->d_order);
+  cudaFree(b->d_sync);
   delete b;
 }
 
 void lists_of(const ocp_batch* b, ocp::TileList* L) {
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < ocp::kNumTileSizes; ++k) {
     L[k].models = b->d_models;
     L[k].tiles = b->d_tiles[k];
     L[k].ntiles = b->ntiles[k];
@@ -82,21 +92,38 @@ cudaError_t upload(ocp_batch* b, double dt, cudaStream_t s) {
   return e;
 }
 
-cudaError_t run(ocp_batch* b, cudaStream_t s) {
-  ocp::TileList L[2];
+cudaError_t run_cfg(ocp_batch* b, const ocp::LaunchCfg& cfg, cudaStream_t s) {
+  ocp::TileList L[ocp::kNumTileSizes];
   lists_of(b, L);
   ocp::ModelArgs unused{};
-  return ocp::launch_tiles(b->nb, L, unused, b->cfg, b->sms, s);
+  if (cfg.ordered == 0) return ocp::launch_tiles(b->nb, L, unused, cfg, b->sms, s);
+  const int ti = ocp::tile_index(cfg.tpb[1]);
+  if (ti < 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned) * (1 + 2 * b->nsync_tiles), s);
+  if (e != cudaSuccess) return e;
+  ocp::OrderedList O{};
+  O.models = b->d_models;
+  O.order = b->d_order;
+  O.tile_start = b->d_tile_start[ti];
+  O.nmodels = (int)b->grids.size();
+  O.nitems = b->ntiles[ti];
+  O.counter = b->d_sync;
+  O.flag_cell = reinterpret_cast<int*>(b->d_sync + 1);
+  O.flag_face = reinterpret_cast<int*>(b->d_sync + 1 + b->nsync_tiles);
+  return ocp::launch_ordered(b->nb, L, O, unused, cfg, b->sms, s);
 }
+
+cudaError_t run(ocp_batch* b, cudaStream_t s) { return run_cfg(b, b->cfg, s); }
 
 ocp_status check_shape(const ocp_launch_shape* sh) {
   if (!sh) return ocp::report(OCP_ERR_INVALID_ARG, "launch shape is NULL");
   for (int s = 0; s < 3; ++s) {
-    if (sh->cells_per_tile[s] != 128 && sh->cells_per_tile[s] != 256)
-      return ocp::report(OCP_ERR_INVALID_ARG, "cells_per_tile must be 128 or 256");
+    if (ocp::tile_index(sh->cells_per_tile[s]) < 0)
+      return ocp::report(OCP_ERR_INVALID_ARG, "cells_per_tile must be 32, 64, 128 or 256");
     if (sh->ctas_per_sm[s] < 0 || sh->ctas_per_sm[s] > 64)
       return ocp::report(OCP_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
   }
+  if (sh->ordered < 0 || sh->ordered > 2) return ocp::report(OCP_ERR_INVALID_ARG, "ordered must be 0, 1 or 2");
   return OCP_OK;
 }
 
@@ -119,22 +146,38 @@ ocp_status ocp_batch_create(ocp_grid* const* grids, int n, ocp_batch** out) {
   b->nb = grids[0]->prm.nb;
   b->sms = grids[0]->sms;
   b->grids.assign(grids, grids + n);
-  b->cfg = grids[0]->cfg;
+  for (int m = 0; m < n; ++m) b->ncell += grids[m]->prm.N;
+  b->cfg = ocp::default_cfg(b->ncell, b->sms);    // until tuned or set
   // largest models first
   std::vector<int> order(n);
   for (int m = 0; m < n; ++m) order[m] = m;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return grids[a]->prm.N > grids[c]->prm.N; });
-  std::vector<int2> tiles[2];
-  const int tpb[2] = {128, 256};
-  for (int k = 0; k < 2; ++k)
+  std::vector<int2> tiles[ocp::kNumTileSizes];
+  for (int k = 0; k < ocp::kNumTileSizes; ++k)
     for (int m : order)
-      for (long long c0 = 0; c0 < grids[m]->prm.N; c0 += tpb[k]) tiles[k].push_back(make_int2(m, (int)c0));
-  for (int m = 0; m < n; ++m) b->ncell += grids[m]->prm.N;
+      for (long long c0 = 0; c0 < grids[m]->prm.N; c0 += ocp::kTileSizes[k])
+        tiles[k].push_back(make_int2(m, (int)c0));
   Guard guard(b->device);
   cudaError_t e = guard.err;
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_models, sizeof(ocp::ModelArgs) * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_models, sizeof(ocp::ModelArgs) * n);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+  // the ordered launch's model order and per-model tile offsets
+  std::vector<long long> tstart[ocp::kNumTileSizes];
+  for (int k = 0; k < ocp::kNumTileSizes; ++k) {
+    tstart[k].push_back(0);
+    for (int m : order) tstart[k].push_back(tstart[k].back() + (grids[m]->prm.N + ocp::kTileSizes[k] - 1) / ocp::kTileSizes[k]);
+  }
+  b->nsync_tiles = tstart[0].back();
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_order, sizeof(int) * n);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_sync, sizeof(unsigned) * (1 + 2 * b->nsync_tiles));
+  for (int k = 0; k < ocp::kNumTileSizes && e == cudaSuccess; ++k) {
+    e = cudaMalloc((void**)&b->d_tile_start[k], sizeof(long long) * tstart[k].size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->d_tile_start[k], tstart[k].data(), sizeof(long long) * tstart[k].size(),
+                     cudaMemcpyHostToDevice);
+  }
+  for (int k = 0; k < ocp::kNumTileSizes && e == cudaSuccess; ++k) {
     b->ntiles[k] = (int)tiles[k].size();
     e = cudaMalloc((void**)&b->d_tiles[k], sizeof(int2) * tiles[k].size());
     if (e == cudaSuccess)
@@ -222,6 +265,7 @@ ocp_status ocp_batch_set_shape(ocp_batch* b, const ocp_launch_shape* sh) {
     b->cfg.tpb[s] = sh->cells_per_tile[s];
     b->cfg.ctas_per_sm[s] = sh->ctas_per_sm[s];
   }
+  b->cfg.ordered = sh->ordered;
   if (b->exec) {                       // the captured graph has the old shape
     Guard guard(b->device);
     cudaDeviceSynchronize();
@@ -237,6 +281,7 @@ ocp_status ocp_batch_get_shape(const ocp_batch* b, ocp_launch_shape* sh) {
     sh->cells_per_tile[s] = b->cfg.tpb[s];
     sh->ctas_per_sm[s] = b->cfg.ctas_per_sm[s];
   }
+  sh->ordered = b->cfg.ordered;
   return OCP_OK;
 }
 
@@ -251,19 +296,18 @@ ocp_status ocp_batch_tune(ocp_batch* b, double dt, int reps, ocp_launch_shape* b
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int tpbs[2] = {128, 256};
   const int ctas[6] = {0, 1, 2, 4, 8, 16};
-  ocp::TileList L[2];
+  ocp::TileList L[ocp::kNumTileSizes];
   lists_of(b, L);
   ocp::ModelArgs unused{};
   ocp::LaunchCfg cur = b->cfg;
   for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
     float best_ms = 1e30f;
     ocp::LaunchCfg pick = cur;
-    for (int ti = 0; ti < 2 && e == cudaSuccess; ++ti)
+    for (int ti = 0; ti < ocp::kNumTileSizes && e == cudaSuccess; ++ti)
       for (int ci = 0; ci < 6 && e == cudaSuccess; ++ci) {
         ocp::LaunchCfg c = cur;
-        c.tpb[stage] = tpbs[ti];
+        c.tpb[stage] = ocp::kTileSizes[ti];
         c.ctas_per_sm[stage] = ctas[ci];
         std::vector<float> t;
         for (int r = 0; r < reps + 1 && e == cudaSuccess; ++r) {
@@ -273,11 +317,10 @@ ocp_status ocp_batch_tune(ocp_batch* b, double dt, int reps, ocp_launch_shape* b
           if (e == cudaSuccess) e = cudaEventRecord(e0, s);
           // run only `stage`: the other stages get an empty grid via a copy with zero tiles
           if (e == cudaSuccess) {
-            ocp::TileList Ls[2] = {L[0], L[1]};
             ocp::LaunchCfg only = one;
             for (int q = 0; q < 3; ++q)
               if (q != stage) only.ctas_per_sm[q] = -1;
-            e = ocp::launch_tiles(b->nb, Ls, unused, only, b->sms, s);
+            e = ocp::launch_tiles(b->nb, L, unused, only, b->sms, s);
           }
           if (e == cudaSuccess) e = cudaEventRecord(e1, s);
           if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -295,6 +338,45 @@ ocp_status ocp_batch_tune(ocp_batch* b, double dt, int reps, ocp_launch_shape* b
       }
     cur = pick;
   }
+  // then the whole pass: the three launches as tuned against the ordered
+  // launches (modes 1 and 2, every tile size, occupancy-sized or 1, 2, 4
+  // CTAs per SM); the fastest is kept
+  auto time_pass = [&](const ocp::LaunchCfg& c, float& med) {
+    std::vector<float> t;
+    for (int r = 0; r < reps + 1 && e == cudaSuccess; ++r) {
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = run_cfg(b, c, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) t.push_back(ms);
+    }
+    if (e == cudaSuccess) {
+      std::sort(t.begin(), t.end());
+      med = t[t.size() / 2];
+    }
+  };
+  if (e == cudaSuccess) {
+    float best_ms = 1e30f;
+    time_pass(cur, best_ms);
+    const int octas[4] = {0, 1, 2, 4};
+    ocp::LaunchCfg base = cur;
+    for (int mode = 1; mode <= 2 && e == cudaSuccess; ++mode)
+      for (int ti = 0; ti < ocp::kNumTileSizes && e == cudaSuccess; ++ti)
+        for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {
+          ocp::LaunchCfg c = base;
+          c.ordered = mode;
+          c.tpb[1] = ocp::kTileSizes[ti];
+          c.ctas_per_sm[1] = octas[ci];
+          float ms = 1e30f;
+          time_pass(c, ms);
+          if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            cur = c;
+          }
+        }
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return ocp::report(OCP_ERR_CUDA, "ocp_batch_tune: %s", cudaGetErrorString(e));
@@ -303,6 +385,7 @@ ocp_status ocp_batch_tune(ocp_batch* b, double dt, int reps, ocp_launch_shape* b
     sh.cells_per_tile[q] = cur.tpb[q];
     sh.ctas_per_sm[q] = cur.ctas_per_sm[q];
   }
+  sh.ordered = cur.ordered;
   if (best) *best = sh;
   return ocp_batch_set_shape(b, &sh);
 }
@@ -325,6 +408,17 @@ ocp_status ocp_grid_set_shape(ocp_grid* g, const ocp_launch_shape* sh) {
     g->cfg.tpb[s] = sh->cells_per_tile[s];
     g->cfg.ctas_per_sm[s] = sh->ctas_per_sm[s];
   }
+  g->cfg.ordered = sh->ordered;
+  return OCP_OK;
+}
+
+ocp_status ocp_grid_get_shape(const ocp_grid* g, ocp_launch_shape* sh) {
+  if (!g || !sh) return ocp::report(OCP_ERR_INVALID_ARG, "grid and shape are required");
+  for (int s = 0; s < 3; ++s) {
+    sh->cells_per_tile[s] = g->cfg.tpb[s];
+    sh->ctas_per_sm[s] = g->cfg.ctas_per_sm[s];
+  }
+  sh->ordered = g->cfg.ordered;
   return OCP_OK;
 }
 

@@ -15,6 +15,12 @@ cudaError_t launch_linearize_scratch(const ocp_grid* g, double* scratch, const d
                                      const int8_t* f_new, const double* u_old, const int8_t* f_old, double dt,
                                      double* res, double* val, double* face_flux, cudaStream_t s);
 ocp_status report(ocp_status st, const char* fmt, ...);
+// Device address of the no-allocation entry point's library array on the
+// current device; the lookup loads the array there (reserving it).
+cudaError_t static_scratch_address(double** out);
+// Loads the linearisation kernels for nb x nb blocks onto the current device
+// (under lazy module loading their first launch would otherwise load them).
+cudaError_t preload_linearize(int nb);
 cudaError_t launch_perf_wi(ocp_grid* g, const double* lnk, cudaStream_t s);
 int64_t solver_work_doubles(const ocp_grid* g);
 
@@ -43,6 +49,9 @@ ocp_status bicgstab_run(ocp_grid* g, const double* val, const WellSchur* ws, con
                         cudaStream_t s, int nbs = 0);
 cudaError_t launch_tiles(int nb, const TileList* lists, const ModelArgs& single, const LaunchCfg& cfg,
                          int sms, cudaStream_t s);
+// The ordered (persistent) launch; O.nitems holds the number of tiles.
+cudaError_t launch_ordered(int nb, const TileList* lists, OrderedList O, const ModelArgs& single,
+                           const LaunchCfg& cfg, int sms, cudaStream_t s);
 ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
                      const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
                      double* face_flux);

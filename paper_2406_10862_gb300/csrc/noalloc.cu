@@ -8,22 +8,28 @@
 // inputs and outputs; this entry point itself calls no cudaMalloc, cudaFree
 // or any allocating routine.
 //
-// The array holds kStaticScratchDoubles doubles (32 MiB).  Every GPU that
-// loads the library holds it until the process exits.  The scratch needs 100
-// doubles per cell, so grids of at most kStaticScratchDoubles / 100 = 41 943
-// cells are accepted; larger grids are rejected with OCP_ERR_INVALID_ARG.
+// The array holds kStaticScratchDoubles doubles (32 MiB).  The scratch needs
+// 100 doubles per cell, so grids of at most kStaticScratchDoubles / 100 =
+// 41 943 cells are accepted; larger grids are rejected with
+// OCP_ERR_INVALID_ARG.
 //
-// In host code the array's name is only a host-side stand-in, not a device
-// address: the device address is looked up with cudaGetSymbolAddress, once
-// per device, with that device current, on the first call made on it.  That
-// first call per device should therefore come before any stream capture.
+// When the array is reserved: with CUDA's lazy module loading (the default)
+// the array and the kernels are only loaded onto a device when they are first
+// used there, and loading them allocates device memory.  So ocp_grid_create,
+// which allocates anyway, does that first use: on the grid's device it looks
+// up the array's device address with cudaGetSymbolAddress (which loads the
+// array, reserving its 32 MiB on that device until the process exits) and
+// loads the linearisation kernels, and it keeps the address in the grid.  In
+// host code the array's name is only a host-side stand-in, never a device
+// address; device code could name it directly, host code uses the address.
+// A device reset (cudaDeviceReset) invalidates every grid on that device, and
+// with it the address.
 //
 // Every call shares the one array and leaves its contents behind.  Nothing
 // in it has to start at zero: each entry a call reads was written earlier in
 // the same call.  Calls that overlap on the GPU (on different streams, or on
 // different grids at the same time) race on the array and must not be made.
 #include <cmath>
-#include <mutex>
 
 #include "kernels.cuh"
 #include "ocp_internal.cuh"
@@ -31,14 +37,23 @@
 namespace {
 
 constexpr long long kStaticScratchDoubles = 4LL * 1024 * 1024;   // 32 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
-std::mutex g_mutex;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
-
 }  // namespace
+
+namespace ocp {
+
+// Device address of the array on the current device (loads it there).
+cudaError_t static_scratch_address(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  *out = (e == cudaSuccess) ? static_cast<double*>(p) : nullptr;
+  if (e == cudaSuccess && !p) e = cudaErrorInvalidSymbol;
+  return e;
+}
+
+}  // namespace ocp
 
 extern "C" ocp_status ocp_linearize_noalloc(ocp_grid* g, const double* u_new, const int8_t* flag_new,
                                             const double* u_old, const int8_t* flag_old, double dt,
@@ -55,31 +70,17 @@ extern "C" ocp_status ocp_linearize_noalloc(ocp_grid* g, const double* u_new, co
     return ocp::report(OCP_ERR_INVALID_ARG,
                        "ocp_linearize_noalloc: grid has %lld cells but the static scratch holds at most %lld cells",
                        (long long)g->prm.N, kStaticScratchDoubles / (need / g->prm.N));
-  if (g->device < 0 || g->device >= kMaxDevices)
-    return ocp::report(OCP_ERR_UNSUPPORTED, "device ordinal %d out of the supported range", g->device);
+  if (!g->d_static_scratch)
+    return ocp::report(OCP_ERR_CUDA, "ocp_linearize_noalloc: no device address for the static scratch");
 
   int prev = -1;
   cudaError_t e = cudaGetDevice(&prev);
   if (e == cudaSuccess && prev != g->device) e = cudaSetDevice(g->device);
   if (e != cudaSuccess) return ocp::report(OCP_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-
-  double* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[g->device]) {
-      // set-up, once per device, with that device current
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_static_scratch);
-      if (e == cudaSuccess && p) g_scratch_addr[g->device] = static_cast<double*>(p);
-    }
-    scratch = g_scratch_addr[g->device];
-  }
-  if (e == cudaSuccess && scratch)
-    e = ocp::launch_linearize_scratch(g, scratch, u_new, flag_new, u_old, flag_old, dt, residual, bsr_val,
-                                      face_flux, (cudaStream_t)stream);
+  e = ocp::launch_linearize_scratch(g, g->d_static_scratch, u_new, flag_new, u_old, flag_old, dt, residual,
+                                    bsr_val, face_flux, (cudaStream_t)stream);
   if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
   if (e != cudaSuccess)
     return ocp::report(OCP_ERR_CUDA, "ocp_linearize_noalloc: %s", cudaGetErrorString(e));
-  if (!scratch) return ocp::report(OCP_ERR_CUDA, "ocp_linearize_noalloc: no device address for the scratch");
   return OCP_OK;
 }

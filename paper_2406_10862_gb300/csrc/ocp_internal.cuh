@@ -28,7 +28,7 @@ enum : int { kStatNonFinite = 1, kStatBadFlag = 2, kStatTimeout = 4, kStatBadCon
 // Preprocessed PVT table: knots and, per linear piece k, value and slope of
 // b_o = 1/B_o, 1/mu_o, b_g = 1/B_g, 1/mu_g and R_s versus p, plus the inverse
 // piece p(R_s) for undersaturated oil.  Filled on the host at set-up.
-struct Table {
+struct alignas(16) Table {    // 16-byte size and alignment: one bulk copy moves it
   int nrow;
   double p[kMaxRows];
   double rs[kMaxRows];
@@ -74,11 +74,37 @@ struct Perf {
 };
 
 // Launch shape of the three linearisation stages (cell, face, assemble):
-// cells per tile (128 or 256) and CTAs per SM (0: one CTA per tile).
+// cells per tile (one of kTileSizes; a CTA has one thread per cell of its
+// tile) and CTAs per SM (0: one CTA per tile).
 struct LaunchCfg {
   int tpb[3];
   int ctas_per_sm[3];
+  int ordered;     // 0: three launches; 1: cell launch + ordered face/assembly launch
+                   // (tile size tpb[1], grid ctas_per_sm[1]); 2: one ordered launch
 };
+constexpr int kNumTileSizes = 4;
+constexpr int kTileSizes[kNumTileSizes] = {32, 64, 128, 256};
+inline int tile_index(int tpb) {
+  for (int t = 0; t < kNumTileSizes; ++t)
+    if (kTileSizes[t] == tpb) return t;
+  return -1;
+}
+// Default launch shape of one grid of N cells on an SM count `sms`: the
+// largest tiles (128 for the register-heavy cell and face stages, 256 for
+// assembly) that still give every SM at least two CTAs, down to 32-cell
+// tiles, so that a small grid spreads its FP64 work over many SMs instead of
+// a few.
+inline LaunchCfg default_cfg(long long N, int sms) {
+  LaunchCfg c;
+  for (int s = 0; s < 3; ++s) {
+    int t = s < 2 ? 128 : 256;
+    while (t > 32 && N < 2LL * t * (sms > 0 ? sms : 1)) t /= 2;
+    c.tpb[s] = t;
+    c.ctas_per_sm[s] = 0;
+  }
+  c.ordered = 0;
+  return c;
+}
 
 }  // namespace ocp
 
@@ -101,6 +127,8 @@ struct ocp_grid {
   int32_t* d_well_first;     // [nwell+1] perforations of well w: well_first[w] .. well_first[w+1]
   int* d_status;             // sticky device status word
   double* d_scratch;         // per-cell scratch of the linearisation
+  double* d_static_scratch;  // the no-allocation entry point's library array on this device
+  unsigned* d_sync;          // ordered launch: item counter, then cell and face flags per 32-cell tile
   double* d_pn;              // per-cell data of the (P, N) path, allocated on its first use
   int8_t* d_pn_flag;
   cudaStream_t solve_cap;    // private stream on which the solver's iterations are captured
@@ -146,6 +174,22 @@ struct TileList {
   int ntiles;
 };
 
+// The work list of the ordered (persistent) launch of the linearisation.
+// With models == nullptr: the single model passed by value.  Otherwise the
+// models in the order order[0..nmodels); tile_start[j] = tiles of the models
+// before the j-th (so its tile flags start there, and its items at that
+// number times the items per tile).
+struct OrderedList {
+  const ModelArgs* models;
+  const int* order;
+  const long long* tile_start;   // [nmodels + 1]
+  int nmodels;
+  long long nitems;
+  unsigned* counter;             // next item (zero before the launch)
+  int* flag_cell;                // per tile: cell stage done (zero before the launch)
+  int* flag_face;                // per tile: face stage done (zero before the launch)
+};
+
 }  // namespace ocp
 
 namespace ocp {
@@ -186,6 +230,54 @@ __device__ __forceinline__ long long row_start_ijk(const Params& P, long long c,
   const long long k0 = c < nxy ? c : nxy;                  // ... with k == 0
   const long long kL = c > N - nxy ? c - (N - nxy) : 0;    // ... with k == nz-1
   return 7 * c - (i0 + iL + j0 + jL + k0 + kL);
+}
+
+// ------------------------------------------------------- PVT table staging
+// Polls an mbarrier's phase `parity` at most 2^20 times; false if it never
+// completed.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (unsigned it = 0; it < (1u << 20); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Copies the PVT table of a model into the CTA's shared memory with one
+// bulk asynchronous copy (the TMA unit) that completes on the mbarrier
+// `bar`; every thread of the CTA calls it and returns once the table has
+// arrived.  `uses` counts the loads this CTA has made with `bar` (the
+// mbarrier's phase).  The table is 16-byte aligned and sized (cudaMalloc'd,
+// alignas(16)), as the copy requires.  The wait is bounded: a thread past
+// its limit records kStatTimeout and waits once more for the copy in flight.
+// Callers that reload the table must make sure no thread still reads the
+// previous one (a barrier before the call).
+__device__ __forceinline__ void load_table(Table& T, const Table* src, unsigned long long& bar, unsigned& uses,
+                                           int* status) {
+  const unsigned ubar = (unsigned)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) {
+    if (uses == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ubar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ubar), "r"((unsigned)sizeof(Table))
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(&T)),
+                 "l"(src), "r"((unsigned)sizeof(Table)), "r"(ubar)
+                 : "memory");
+  }
+  __syncthreads();                       // the mbarrier is initialised before anyone waits on it
+  if (!mbar_wait(ubar, uses & 1u)) {
+    atomicOr(status, kStatTimeout);
+    mbar_wait(ubar, uses & 1u);
+  }
+  ++uses;
 }
 
 // ---------------------------------------------------------------- bit tricks

@@ -332,11 +332,12 @@ __global__ void __launch_bounds__(256) vjp_kernel(Params P, const Table* __restr
                                                   const Perf* __restrict__ perf, double scale,
                                                   const double* __restrict__ lam,
                                                   double* __restrict__ g_unew, double* __restrict__ g_uold,
-                                                  double* __restrict__ g_lnk, double* __restrict__ g_phi) {
+                                                  double* __restrict__ g_lnk, double* __restrict__ g_phi,
+                                                  int* __restrict__ status) {
   __shared__ Table T;
-  for (int i = threadIdx.x; i < (int)(sizeof(Table) / 8); i += blockDim.x)
-    reinterpret_cast<double*>(&T)[i] = reinterpret_cast<const double*>(gT)[i];
-  __syncthreads();
+  __shared__ unsigned long long bar;
+  unsigned uses = 0;
+  load_table(T, gT, bar, uses, status);
   const long long N = P.N;
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= N) return;
@@ -516,11 +517,11 @@ cudaError_t launch_vjp(const ocp_grid* g, const double* u_new, const int8_t* f_n
   if (P.nb == 3)
     vjp_kernel<3><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, val, face_flux,
                                          g->d_wlnk, g->d_perf_of_cell, g->d_perf, scale, lam, g_unew, g_uold,
-                                         g_lnk, g_phi);
+                                         g_lnk, g_phi, g->d_status);
   else
     vjp_kernel<2><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, val, face_flux,
                                          g->d_wlnk, g->d_perf_of_cell, g->d_perf, scale, lam, g_unew, g_uold,
-                                         g_lnk, g_phi);
+                                         g_lnk, g_phi, g->d_status);
   return cudaGetLastError();
 }
 

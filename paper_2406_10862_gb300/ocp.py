@@ -29,6 +29,7 @@ EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_patt
            "ocp_linearize_noalloc", "ocp_probe_fp64", "ocp_batch_create", "ocp_batch_destroy",
            "ocp_batch_set_io", "ocp_batch_linearize", "ocp_batch_graph_launch", "ocp_batch_tune",
            "ocp_batch_set_shape", "ocp_batch_get_shape", "ocp_batch_get_status", "ocp_grid_set_shape",
+           "ocp_grid_get_shape",
            "ocp_solver_work_doubles", "ocp_bicgstab", "ocp_newton_update", "ocp_well_rates_vjp",
            "ocp_grid_update_perm", "ocp_coupling_work_ints", "ocp_coupling_components", "ocp_linearize_wells",
            "ocp_bicgstab_wells", "ocp_well_update", "ocp_residual_norms", "ocp_linearize_pn", "ocp_pn_update",
@@ -90,7 +91,7 @@ class _BatchIO(ctypes.Structure):
 
 
 class _Shape(ctypes.Structure):
-    _fields_ = [("cells_per_tile", ctypes.c_int * 3), ("ctas_per_sm", ctypes.c_int * 3)]
+    _fields_ = [("cells_per_tile", ctypes.c_int * 3), ("ctas_per_sm", ctypes.c_int * 3), ("ordered", ctypes.c_int)]
 
 
 _lib = None
@@ -133,6 +134,7 @@ def load(build_if_missing: bool = False):
     lib.ocp_batch_get_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
     lib.ocp_batch_get_status.argtypes = [vp, vp]
     lib.ocp_grid_set_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
+    lib.ocp_grid_get_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
     lib.ocp_solver_work_doubles.argtypes = [vp]
     lib.ocp_solver_work_doubles.restype = ctypes.c_int64
     lib.ocp_bicgstab.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp,
@@ -286,14 +288,19 @@ class Grid:
         return row_ptr, col_idx
 
     # ------------------------------------------------------------ calls
+    def _flags(self, flag_new, flag_old):
+        """Phase-state flags: required with three phases; with two phases
+        optional (unused by the library), each checked when given."""
+        required = self.nb == 3
+        self._t(flag_new, self.N, torch.int8, "flag_new", allow_none=not required)
+        self._t(flag_old, self.N, torch.int8, "flag_old", allow_none=not required)
+
     def linearize(self, u_new, flag_new, u_old, flag_old, dt, residual=None, bsr_val=None,
                   face_flux=None, want_face_flux=False, stream=None):
         N, nb = self.N, self.nb
         self._t(u_new, nb * N, torch.float64, "u_new")
         self._t(u_old, nb * N, torch.float64, "u_old")
-        if nb == 3 or flag_new is not None:
-            self._t(flag_new, N, torch.int8, "flag_new")
-            self._t(flag_old, N, torch.int8, "flag_old")
+        self._flags(flag_new, flag_old)
         residual = residual if residual is not None else self.empty(nb * N)
         bsr_val = bsr_val if bsr_val is not None else self.empty(self.nnzb * nb * nb)
         if face_flux is None and want_face_flux:
@@ -313,9 +320,7 @@ class Grid:
         N, nb = self.N, self.nb
         self._t(u_new, nb * N, torch.float64, "u_new")
         self._t(u_old, nb * N, torch.float64, "u_old")
-        if nb == 3 or flag_new is not None:
-            self._t(flag_new, N, torch.int8, "flag_new")
-            self._t(flag_old, N, torch.int8, "flag_old")
+        self._flags(flag_new, flag_old)
         self._t(residual, nb * N, torch.float64, "residual")
         self._t(bsr_val, self.nnzb * nb * nb, torch.float64, "bsr_val")
         self._t(face_flux, 3 * nb * N, torch.float64, "face_flux", allow_none=True)
@@ -337,6 +342,9 @@ class Grid:
     def adjoint_vjp(self, u_new, flag_new, u_old, flag_old, dt, bsr_val, face_flux, lam,
                     want=("unew", "uold", "lnk", "phi"), out=None, stream=None):
         N, nb = self.N, self.nb
+        self._t(u_new, nb * N, torch.float64, "u_new")
+        self._t(u_old, nb * N, torch.float64, "u_old")
+        self._flags(flag_new, flag_old)
         self._t(lam, nb * N, torch.float64, "lambda")
         out = dict(out or {})
         sizes = {"unew": nb * N, "uold": nb * N, "lnk": N, "phi": N}
@@ -395,9 +403,7 @@ class Grid:
         N, nb, nw, npf = self.N, self.nb, self.nwell, self.nperf
         self._t(u_new, nb * N, torch.float64, "u_new")
         self._t(u_old, nb * N, torch.float64, "u_old")
-        if nb == 3 or flag_new is not None:
-            self._t(flag_new, N, torch.int8, "flag_new")
-            self._t(flag_old, N, torch.int8, "flag_old")
+        self._flags(flag_new, flag_old)
         self._t(p_bh, nw, torch.float64, "p_bh")
         self._t(ctrl, 24 * nw, torch.uint8, "ctrl")
         o = dict(out or {})
@@ -523,9 +529,7 @@ class Grid:
         N, nb = self.N, self.nb
         self._t(u_new, nb * N, torch.float64, "u_new")
         self._t(u_old, nb * N, torch.float64, "u_old")
-        if nb == 3 or flag_new is not None:
-            self._t(flag_new, N, torch.int8, "flag_new")
-            self._t(flag_old, N, torch.int8, "flag_old")
+        self._flags(flag_new, flag_old)
         S = int(px) * int(py) * int(pz)
         nwork = int(lib.ocp_coupling_work_ints(int(px), int(py), int(pz)))
         if S < 1 or nwork < 1:
@@ -543,9 +547,14 @@ class Grid:
         """Launch shape of ocp_linearize on this grid (``ocp_grid_set_shape``)."""
         _check(load().ocp_grid_set_shape(self._h, ctypes.byref(shape_from_dict(d))))
 
+    def get_shape(self):
+        sh = _Shape()
+        _check(load().ocp_grid_get_shape(self._h, ctypes.byref(sh)))
+        return shape_to_dict(sh)
+
 
 def shape_to_dict(sh):
-    return {"cells_per_tile": list(sh.cells_per_tile), "ctas_per_sm": list(sh.ctas_per_sm)}
+    return {"cells_per_tile": list(sh.cells_per_tile), "ctas_per_sm": list(sh.ctas_per_sm), "ordered": sh.ordered}
 
 
 def shape_from_dict(d):
@@ -553,6 +562,7 @@ def shape_from_dict(d):
     for q in range(3):
         sh.cells_per_tile[q] = int(d["cells_per_tile"][q])
         sh.ctas_per_sm[q] = int(d["ctas_per_sm"][q])
+    sh.ordered = int(d.get("ordered", 0))
     return sh
 
 
@@ -624,27 +634,3 @@ def probe_fp64(device=0, reps=3):
     _check(lib.ocp_probe_fp64(int(device), int(reps), ctypes.byref(r)))
     return 2.0 * r.value / 1e9
 
-
-# C names, for callers who prefer the flat interface
-def ocp_grid_create(desc, device=0):
-    return Grid(desc, device)
-
-
-def ocp_linearize(grid, *a, **k):
-    return grid.linearize(*a, **k)
-
-
-def ocp_bsr_spmv(grid, *a, **k):
-    return grid.spmv(*a, **k)
-
-
-def ocp_adjoint_vjp(grid, *a, **k):
-    return grid.adjoint_vjp(*a, **k)
-
-
-def ocp_well_rates(grid, *a, **k):
-    return grid.well_rates(*a, **k)
-
-
-def ocp_get_status(grid, stream=None):
-    return grid.status(stream)

@@ -54,13 +54,21 @@ def test_batch_equals_per_model_bitwise_for_every_shape(nphase):
     batch.set_io(ios)
     shapes = [dict(cells_per_tile=[256, 256, 256], ctas_per_sm=[0, 0, 0]),
               dict(cells_per_tile=[128, 256, 128], ctas_per_sm=[1, 2, 4]),
-              dict(cells_per_tile=[256, 128, 256], ctas_per_sm=[8, 1, 16])]
+              dict(cells_per_tile=[256, 128, 256], ctas_per_sm=[8, 1, 16]),
+              dict(cells_per_tile=[32, 64, 32], ctas_per_sm=[0, 3, 0]),
+              # ordered (persistent) launches: face + assembly, then cell + face + assembly
+              dict(cells_per_tile=[128, 128, 256], ctas_per_sm=[0, 0, 0], ordered=1),
+              dict(cells_per_tile=[64, 32, 256], ctas_per_sm=[2, 1, 0], ordered=1),
+              dict(cells_per_tile=[128, 128, 256], ctas_per_sm=[0, 0, 0], ordered=2),
+              dict(cells_per_tile=[128, 256, 128], ctas_per_sm=[0, 1, 0], ordered=2),
+              dict(cells_per_tile=[128, 32, 128], ctas_per_sm=[0, 2, 0], ordered=2)]
     for k, sh in enumerate(shapes):
         batch.set_shape(sh)
         for io in ios:
             io["residual"].fill_(np.nan)
             io["bsr_val"].fill_(np.nan)
-        batch.linearize(1.0, graph=(k == 2))
+            io["face_flux"].fill_(np.nan)
+        batch.linearize(1.0, graph=(k in (2, 6)))
         assert batch.status() == 0
         for io, (r, v, f) in zip(ios, ref):
             assert same_bits(io["residual"], r) and same_bits(io["bsr_val"], v) and same_bits(io["face_flux"], f)
@@ -100,7 +108,8 @@ def test_tuner_returns_a_valid_shape_and_keeps_results():
     batch = O.Batch(grids)
     batch.set_io(ios)
     best = batch.tune(1.0, reps=2)
-    assert all(t in (128, 256) for t in best["cells_per_tile"]) and all(0 <= c <= 16 for c in best["ctas_per_sm"])
+    assert all(t in (32, 64, 128, 256) for t in best["cells_per_tile"])
+    assert all(0 <= c <= 16 for c in best["ctas_per_sm"]) and best["ordered"] in (0, 1, 2)
     assert batch.get_shape() == best
     batch.linearize(1.0, graph=True)
     torch.cuda.synchronize()
@@ -123,4 +132,6 @@ def test_batch_status_and_errors():
     with pytest.raises(O.OcpError):
         O.Batch([grids[0], O.Grid(g2)])            # mixed block sizes
     with pytest.raises(O.OcpError):
-        batch.set_shape(dict(cells_per_tile=[64, 256, 256], ctas_per_sm=[0, 0, 0]))
+        batch.set_shape(dict(cells_per_tile=[48, 256, 256], ctas_per_sm=[0, 0, 0]))
+    with pytest.raises(O.OcpError):
+        batch.set_shape(dict(cells_per_tile=[64, 256, 256], ctas_per_sm=[0, 0, 0], ordered=3))

@@ -87,6 +87,35 @@ def test_linearize_is_deterministic():
         assert np.array_equal(x.view(np.int64), y.view(np.int64))
 
 
+@pytest.mark.parametrize("nphase,shape", [(3, (13, 11, 7)), (3, (100, 3, 2)), (2, (9, 30, 5)), (3, (1, 1, 1)),
+                                          (3, (40, 40, 3))])
+def test_launch_shapes_are_bitwise_identical(nphase, shape):
+    """Every launch shape of one grid -- tile sizes 32 to 256, one CTA per
+    tile or persistent grids, three launches or the ordered launches (face
+    stage and assembly in one persistent launch after the cell stage, or
+    everything in one) -- gives the same bits, and those match the oracle."""
+    O = ocp()
+    g, s = W.tiny(*shape, nphase=nphase, seed=sum(shape) + 7, frac_unsat=0.3 if nphase == 3 else 0.0)
+    grid = O.Grid(g)
+    ref = gpu_linearize(grid, s)
+    assert ref[3] == 0
+    o = orc(g, s)
+    assert_scaled_close(ref[0], o["R"], o["R_mag"], RTOL_R, "residual")
+    assert_scaled_close(ref[1], o["val"], o["val_mag"], RTOL_J, "jacobian")
+    shapes = [dict(cells_per_tile=[128, 128, 256], ctas_per_sm=[0, 0, 0], ordered=0),
+              dict(cells_per_tile=[32, 64, 128], ctas_per_sm=[2, 0, 4], ordered=0)]
+    for mode in (1, 2):
+        for t in (32, 64, 128, 256):
+            shapes.append(dict(cells_per_tile=[t, t, 256], ctas_per_sm=[0, 0, 0], ordered=mode))
+        shapes.append(dict(cells_per_tile=[64, 128, 256], ctas_per_sm=[0, 1, 0], ordered=mode))
+    for sh in shapes:
+        grid.set_shape(sh)
+        got = gpu_linearize(grid, s)
+        assert got[3] == 0, sh
+        for x, y in zip(got[:3], ref[:3]):
+            assert np.array_equal(x.view(np.int64), y.view(np.int64)), sh
+
+
 @pytest.mark.parametrize("nphase", [3, 2])
 @pytest.mark.parametrize("alpha,beta,transpose", [(1.0, 0.0, False), (-0.7, 0.3, False), (2.5, 0.0, True),
                                                   (1.0, 1.0, True)])
