@@ -127,3 +127,72 @@ def global_max(v: torch.Tensor, group=None):
     t = v.max().reshape(1).to(torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     return t[0]
+
+
+def block_jacobi(diag_blocks: torch.Tensor):
+    """The block-Jacobi preconditioner of the owned rows: z = D^-1 r with D
+    the owned cells' diagonal blocks (n_own, nb, nb); no communication."""
+    inv = torch.linalg.inv(diag_blocks)
+
+    def apply(r: torch.Tensor):
+        nb = inv.shape[-1]
+        return torch.einsum("cij,cj->ci", inv, r.view(-1, nb)).reshape(-1)
+    return apply
+
+
+def bicgstab(matvec, precond, b: torch.Tensor, x: torch.Tensor, dot, rtol: float, maxit: int):
+    """Left-preconditioned BiCGSTAB on the owned part of the unknowns (the
+    Krylov method of the linear solver, Sec. 3.3.3 and Sec. 5.1, with the
+    block-Jacobi preconditioner the library's solver also uses):
+    solves M^-1 A x = M^-1 b.  ``matvec(v)`` returns the owned rows of A v
+    for owned v (a distributed product exchanges the ghost layers inside);
+    ``precond`` applies M^-1 to owned rows; ``dot`` is the global dot product
+    of owned vectors (an Allreduce across slabs).  With one domain these are
+    the plain product and dot, so the partitioned iterates equal the
+    single-domain ones up to the summation order of the dots.  Stops when
+    ||M^-1 (b - A x)|| <= rtol ||M^-1 b|| or after maxit iterations.
+    Returns (x, iterations, relative residual)."""
+    r = precond(b - matvec(x))
+    nb0 = float(torch.sqrt(dot(precond(b), precond(b))))
+    r0 = r.clone()
+    rho = alpha = omega = 1.0
+    v = torch.zeros_like(b)
+    p = torch.zeros_like(b)
+    it = 0
+    res = float(torch.sqrt(dot(r, r))) / (nb0 if nb0 > 0 else 1.0)
+    while it < maxit and res > rtol:
+        rho_new = float(dot(r0, r))
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = precond(matvec(p))
+        alpha = rho_new / float(dot(r0, v))
+        s = r - alpha * v
+        t = precond(matvec(s))
+        tt = float(dot(t, t))
+        omega = float(dot(t, s)) / tt if tt > 0 else 0.0
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho = rho_new
+        it += 1
+        res = float(torch.sqrt(dot(r, r))) / (nb0 if nb0 > 0 else 1.0)
+    return x, it, res
+
+
+def distributed_bicgstab(apply_sub, diag_blocks: torch.Tensor, b_own: torch.Tensor, x_own: torch.Tensor,
+                         slab: Slab, nb: int, n_sub: int, rtol: float, maxit: int, group=None):
+    """BiCGSTAB over slabs: ``apply_sub`` is the sub-grid's block-CSR product
+    (its ghost rows are never used), ``diag_blocks`` the owned cells' diagonal
+    blocks.  Each product first exchanges the ghost layers of its operand
+    (point to point, Sec. 3.4.1); each dot product is an Allreduce of the
+    owned parts (Sec. 3.4.2)."""
+    full = torch.zeros(n_sub * nb, dtype=b_own.dtype)
+    own = slice(slab.owned.start * nb, slab.owned.stop * nb)
+
+    def matvec(v):
+        full.zero_()
+        full[own] = v
+        y = distributed_spmv(apply_sub, full, slab, nb, group)
+        return y[own].clone()
+
+    return bicgstab(matvec, block_jacobi(diag_blocks), b_own, x_own,
+                    lambda a, c: global_dot(a, c, group), rtol, maxit)

@@ -143,3 +143,81 @@ def test_distributed_spmv_rows_and_norms(world):
         assert m == float(np.abs(y).max())
         seen[gown] = True
     assert seen.all()
+
+
+def _solver_worker(rank, world, port, out_q, maxit):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle.linearize import linearize
+        from oracle.spmv import bsr_spmv
+        from paper_2406_10862_gb300 import partition as P
+        from paper_2406_10862_gb300 import workloads as W
+        g, s = W.tiny(4, 3, 8, seed=79, frac_unsat=0.3)
+        nb = g.nphase
+        slab = P.slab_of(g.nz, g.nx * g.ny, rank, world)
+        h = P.subgrid(g, slab)
+        cells = slab.global_cells
+        own = slab.owned
+        o = linearize(h, s.u_new[:, cells], s.flag_new[cells], s.u_old[:, cells], s.flag_old[cells], s.dt)
+        apply = lambda v: torch.from_numpy(
+            bsr_spmv(o["row_ptr"], o["col_idx"], o["val"], v.numpy())[0].copy())
+        rp, ci = o["row_ptr"], o["col_idx"]
+        diag = torch.from_numpy(np.stack([o["val"][rp[c] + np.nonzero(ci[rp[c]:rp[c + 1]] == c)[0][0]]
+                                          for c in range(own.start, own.stop)]))
+        b = torch.from_numpy(-o["R"][own].ravel().copy())
+        x, it, res = P.distributed_bicgstab(apply, diag, b, torch.zeros_like(b), slab, nb, len(cells), 0.0,
+                                            maxit)
+        out_q.put((rank, cells[own], x.numpy().copy(), it, res))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,maxit", [(2, 6), (2, 200), (3, 6)])
+def test_distributed_bicgstab_follows_the_single_domain_iterates(world, maxit):
+    """Block-Jacobi BiCGSTAB over slabs (ghost layers of every operand
+    exchanged point to point, every dot product an Allreduce) takes the same
+    iterates as the single-domain solver to rounding (only the dots sum in
+    another order), after a few iterations and at convergence."""
+    from oracle.linearize import linearize
+    from oracle.spmv import bsr_spmv
+    from paper_2406_10862_gb300 import partition as P
+    from paper_2406_10862_gb300 import workloads as W
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_solver_worker, args=(r, world, port, q, maxit)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    g, s = W.tiny(4, 3, 8, seed=79, frac_unsat=0.3)
+    nb = g.nphase
+    o = linearize(g, s.u_new, s.flag_new, s.u_old, s.flag_old, s.dt)
+    rp, ci = o["row_ptr"], o["col_idx"]
+    diag = torch.from_numpy(np.stack([o["val"][rp[c] + np.nonzero(ci[rp[c]:rp[c + 1]] == c)[0][0]]
+                                      for c in range(g.N)]))
+    matvec = lambda v: torch.from_numpy(bsr_spmv(rp, ci, o["val"], v.numpy())[0].copy())
+    b = torch.from_numpy(-o["R"].ravel().copy())
+    x_ref, it_ref, res_ref = P.bicgstab(matvec, P.block_jacobi(diag), b, torch.zeros_like(b),
+                                        lambda a, c: (a * c).sum(), 0.0, maxit)
+    x_ref = x_ref.numpy().reshape(-1, nb)
+    seen = np.zeros(g.N, dtype=bool)
+    scale = np.abs(x_ref).max(axis=0)
+    for rank, gown, x, it, r in res:
+        assert it == it_ref
+        assert np.all(np.abs(x.reshape(-1, nb) - x_ref[gown]) <= 1e-9 * scale)
+        seen[gown] = True
+    assert seen.all()
+    if maxit > 100:
+        assert res_ref < 1e-12
+        # the converged iterate solves the system
+        A = np.zeros((g.N * nb, g.N * nb))
+        for r_ in range(g.N):
+            for k in range(rp[r_], rp[r_ + 1]):
+                A[r_ * nb:(r_ + 1) * nb, ci[k] * nb:(ci[k] + 1) * nb] = o["val"][k]
+        xs = np.linalg.solve(A, b.numpy())
+        assert np.allclose(x_ref.ravel(), xs, rtol=1e-8, atol=1e-10 * np.abs(xs).max())
