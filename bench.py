@@ -42,20 +42,49 @@ def env_int(name, default):
         return default
 
 
-# DRAM bytes (read + write) of one spmv_grid_kernel<3> launch on the
-# 100x100x20 workload from the ncu capture summarised in
-# profiles/layered_box_kernels_full.md, valid for the kernel sources whose
-# hash is given; any change to them makes the figure void (reported null).
-SPMV_TRAFFIC = {"sources_sha256_16": "e67b1c58e0eb034c", "bytes": 105.36e6}
+# Figures that only an ncu capture gives (DRAM bytes, FP64 instruction
+# counts), stored with the SHA-256 (first 16 hex digits) of the sources of
+# the kernels they describe; `stored()` returns them only while those files
+# still hash to the recorded value, and None (reported null) after any change.
+# Captures: profiles/layered_box_lin_vjp_fp64_dram.md (commands there).
+#   fp64_inst_per_cell  FP64 thread instructions per cell (per row for the
+#                       SpMV), summed over the kernels of the phase
+#   fp64_warp_inst_per_cell  FP64 warp instructions per cell: each occupies
+#                       the SM's FP64 pipe for 16 cycles whatever its lanes
+#   dram_bytes          DRAM read + write bytes of one call on the
+#                       100x100x20 workload
+STORED = {
+    "spmv": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": "e67b1c58e0eb034c",
+             "dram_bytes": 105.36e6},
+    "linearize": {"sources": ["linearize.cu", "ocp_internal.cuh"], "sha16": None,
+                  "fp64_inst_per_cell": None, "fp64_warp_inst_per_cell": None, "dram_bytes": None},
+    "vjp": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": None,
+            "fp64_inst_per_cell": None, "fp64_warp_inst_per_cell": None, "dram_bytes": None},
+}
+
+
+def sources_sha16(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2406_10862_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored(name, key):
+    rec = STORED[name]
+    if rec.get("sha16") is None or sources_sha16(rec["sources"]) != rec["sha16"]:
+        return None
+    return rec.get(key)
 
 
 def spmv_traffic():
-    import hashlib
-    h = hashlib.sha256()
-    for f in ("paper_2406_10862_gb300/csrc/spmv_adjoint.cu", "paper_2406_10862_gb300/csrc/ocp_internal.cuh"):
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    return SPMV_TRAFFIC["bytes"] if h.hexdigest()[:16] == SPMV_TRAFFIC["sources_sha256_16"] else None
+    return stored("spmv", "dram_bytes")
+
+
+def lin_fp64_per_cell():
+    return stored("linearize", "fp64_inst_per_cell")
 
 
 def peaks():
@@ -155,11 +184,13 @@ def sub_box(g, s, sx, sy, sz):
     return h, st
 
 
-def oracle_sample_times(g, s, sx=100, sy=100, sz=2, n_rows=2000, seed=9):
-    """Times the CPU oracle on a bounded sample of the workload (a corner
-    sub-box, which contains a producer column) and returns seconds per cell
-    for the linearisation, per row for one SpMV and per cell for the adjoint
-    products, plus a description of the sample."""
+def oracle_sample_step(g, s, sx=20, sy=20, sz=5, seed=9):
+    """Times one whole step of the CPU oracle on a bounded sample of the
+    workload: the corner sub-box [0,sx) x [0,sy) x [0,sz) (it holds the
+    producer column at (4, 4)) linearised once, 50 SpMVs over all of its rows
+    (five seeded vectors in turn, as in the GPU step) and one adjoint pass.
+    Everything reported is timed; nothing is extrapolated.  Returns (seconds,
+    cells of the sample, description)."""
     import numpy as np
 
     from oracle.linearize import linearize
@@ -167,23 +198,19 @@ def oracle_sample_times(g, s, sx=100, sy=100, sz=2, n_rows=2000, seed=9):
 
     h, st = sub_box(g, s, sx, sy, sz)
     nsub = h.N
-    t0 = time.perf_counter()
-    o = linearize(h, st.u_new, st.flag_new, st.u_old, st.flag_old, st.dt)
-    t_lin = (time.perf_counter() - t0) / nsub
     rng = np.random.default_rng(seed)
-    x = rng.normal(size=nsub * 3)
-    rows = rng.choice(nsub, min(n_rows, nsub), replace=False)
-    t0 = time.perf_counter()
-    bsr_spmv(o["row_ptr"], o["col_idx"], o["val"], x, rows=rows)
-    t_spmv = (time.perf_counter() - t0) / len(rows)
+    xs = [rng.normal(size=nsub * 3) for _ in range(5)]
     lam = rng.normal(size=(nsub, 3))
     t0 = time.perf_counter()
+    o = linearize(h, st.u_new, st.flag_new, st.u_old, st.flag_old, st.dt)
+    for k in range(N_SPMV):
+        bsr_spmv(o["row_ptr"], o["col_idx"], o["val"], xs[k % 5])
     linearize(h, st.u_new, st.flag_new, st.u_old, st.flag_old, st.dt, mode="all", lam=lam)
-    t_vjp = (time.perf_counter() - t0) / nsub
-    desc = ("oracle (numpy, 1 thread) on the %dx%dx%d corner sub-box of the workload (%d cells): one "
-            "linearisation, one adjoint pass, and one SpMV over %d sampled rows; scaled per cell to the "
-            "step (1 linearisation + 50 SpMV + 1 adjoint)" % (sx, sy, sz, nsub, len(rows)))
-    return t_lin, t_spmv, t_vjp, desc
+    sec = time.perf_counter() - t0
+    desc = ("oracle (numpy, 1 thread) on the %dx%dx%d corner sub-box of the workload (%d cells), one whole "
+            "step: one linearisation and one adjoint pass (vectorised numpy with dual numbers) and 50 SpMVs "
+            "over all of its rows (the oracle's per-row Python loop, most of the time)" % (sx, sy, sz, nsub))
+    return sec, nsub, desc
 
 
 def _oracle_slab_task(task):
@@ -240,10 +267,6 @@ def host_info():
     return {"machine": platform.machine(), "cpus": os.cpu_count(), "model": model}
 
 
-def cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp):
-    return t_lin + N_SPMV * t_spmv + t_vjp
-
-
 def run_reference(args, rank, world):
     """The CPU oracle as the reference arm: every step is a bounded sample."""
     if rank != 0:
@@ -255,22 +278,24 @@ def run_reference(args, rank, world):
     desc = ""
     # the sample shrinks with the number of steps so the run stays within minutes
     n = args.warmup + args.steps
-    side = 100 if n <= 25 else (50 if n <= 100 else 30)
+    sx, sy, sz = (20, 20, 5) if n <= 30 else (10, 10, 5)
+    nsub = sx * sy * sz
     for k in range(n):
-        t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s, sx=side, sy=side, sz=1,
-                                                         n_rows=max(50, side * 2), seed=k)
+        sec, nsub, desc = oracle_sample_step(g, s, sx, sy, sz, seed=k)
         if k >= args.warmup:
-            per.append(cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp))
-    sec_per_cell = statistics.mean(per)
-    value = 1e-6 / sec_per_cell
-    ms_step = sec_per_cell * g.N * 1e3
+            per.append(sec)
+    ms_step = 1e3 * statistics.mean(per)
+    value = nsub / (ms_step * 1e-3) / 1e6
     line = {
         "impl": "reference", "metric": "Mcell FIM linearisations/s (FP64 residual+BSR Jacobian), % HBM roofline",
         "value": value, "unit": "Mcell/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "layered black-oil box 100x100x20 (200000 cells, 3x3 BSR)",
-                   "step": "linearize + 50 SpMV + adjoint VJP", "global_batch": 1, "parallelism": "cpu"},
+        "config": {"workload": "%dx%dx%d corner sub-box (%d cells) of the layered black-oil box 100x100x20 "
+                               "(3x3 BSR); the rate per cell is the one quoted for the 200000-cell box"
+                               % (sx, sy, sz, nsub),
+                   "step": "linearize + 50 SpMV + adjoint VJP of the sub-box, all timed", "global_batch": 1,
+                   "parallelism": "cpu"},
         "cpu_baseline": {"value": value, "unit": "Mcell/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "Mcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -292,7 +317,11 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
     B.build()
     ocp.load()
-    g, s = W.layered_box()
+    if args.box:
+        nx, ny, nz = (int(a) for a in args.box.lower().split("x"))
+        g, s = W.layered_box(nx=nx, ny=ny, nz=nz)
+    else:
+        g, s = W.layered_box()
     grid = ocp.Grid(g, local_rank)
     N, nb, nnzb = grid.N, grid.nb, grid.nnzb
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
@@ -310,6 +339,23 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.get_device_properties(dev), "L2_cache_size") else 132 * 2 ** 20
     flush = torch.empty(max(4 * l2, 512 * 2 ** 20) // 8, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    # launch shape of the linearisation: given, or autotuned (ocp_batch_tune
+    # on a batch of this one grid, cached in _build/launch_shapes.json), or
+    # the grid's default
+    shape_src = "default"
+    if args.shape:
+        grid.set_shape(json.loads(args.shape))
+        shape_src = "--shape"
+    elif not args.no_tune and not args.profile:
+        from paper_2406_10862_gb300 import autotune
+        one = ocp.Batch([grid])
+        one.set_io([dict(u_new=un, flag_new=fn, u_old=uo, flag_old=fo, residual=r, bsr_val=v, face_flux=ff)])
+        tuned, cached = autotune.tuned_shape(one, s.dt)
+        one.close()
+        grid.set_shape(tuned)
+        shape_src = "autotuned (cached)" if cached else "autotuned"
+    lin_shape = grid.get_shape()
 
     def lin():
         grid.linearize(un, fn, uo, fo, s.dt, r, v, ff)
@@ -551,13 +597,17 @@ def run_gpu(args, rank, world, local_rank):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step_ms,
                     "mode": "pipelined two deep: step k+1's inputs copied in and step k's residual, product and "
                             "gradient copied out on two copy streams while step k computes (its phases replayed "
-                            "as CUDA graphs of the same API calls); wall clock over all steps",
+                            "as CUDA graphs of the same API calls); wall clock over all steps; the Jacobian "
+                            "(98.8 MB) stays on the device, where the SpMVs consume it",
                     "l2": "no flush: each step's working set (Jacobian 98.8 MB + 160 MB scratch) exceeds L2",
                     "results_consistent": e2e_ok,
                     "serial": {"value": world * N / (e2e_serial_ms * 1e-3) / 1e6, "ms_per_step": e2e_serial_ms,
                                "mode": "copy in, per-call API launches, copy out, synchronise; L2 flushed "
                                        "before every step"}},
-            "gpu_launches": args.steps * (3 + N_SPMV + 1),
+            "linearize": lin_line(N, nnzb, statistics.mean(lin), lin_shape, shape_src, hbm_peak),
+            "vjp": vjp_line(N, nnzb, statistics.mean(vjp), hbm_peak),
+            "gpu_launches": args.steps * ((3 if lin_shape["ordered"] == 0 else 2 if lin_shape["ordered"] == 1 else 1)
+                                          + N_SPMV + 1),
             "clocks": clk.summary(),
             "device_status": st,
         }
@@ -574,14 +624,66 @@ def run_gpu(args, rank, world, local_rank):
             line["impec"] = run_impec(dev, local_rank)
             line["coupling"] = run_coupling(dev, local_rank, with_oracle=(world == 1 and not args.no_cpu_baseline))
         if world == 1 and not args.no_cpu_baseline:
-            t_lin, t_spmv, t_vjp, desc = oracle_sample_times(g, s)
-            cpu = 1e-6 / cpu_step_seconds_per_cell(t_lin, t_spmv, t_vjp)
-            line["cpu_baseline"] = {"value": cpu, "unit": "Mcell/s", "cores": 1, "kind": "oracle", "sample": desc}
+            runs = [oracle_sample_step(g, s, seed=k) for k in range(3)]
+            sec = statistics.median(r[0] for r in runs)
+            line["cpu_baseline"] = {"value": runs[0][1] / sec / 1e6, "unit": "Mcell/s", "cores": 1,
+                                    "kind": "oracle", "sample": runs[0][2] + "; median of 3 steps"}
             line["cpu_baseline_all_cores"] = oracle_all_cores()
             line["host"] = host_info()
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# FP64 thread instructions per second of GB300's FP64 pipes: 152 SMs x 2 per
+# clock x 2.07 GHz (a warp instruction occupies an SM's pipe for 16 cycles)
+FP64_INST_PEAK_G = 152 * 2 * 2.07
+
+
+def fp64_part(inst, warp_inst, cells, ms):
+    if inst is None:
+        return {"inst_per_cell": None, "note": "the kernel sources changed since the ncu count was taken"}
+    rate = inst * cells / (ms * 1e-3) / 1e9
+    out = {"inst_per_cell": inst, "achieved_ginst_s": rate, "peak_ginst_s": FP64_INST_PEAK_G,
+           "frac": rate / FP64_INST_PEAK_G,
+           "peak_source": "152 SMs x 2 FP64 lanes per clock x 2.07 GHz"}
+    if warp_inst is not None:
+        out["pipe_frac"] = 32 * warp_inst * cells / (ms * 1e-3) / 1e9 / FP64_INST_PEAK_G
+        out["pipe_frac_meaning"] = "FP64 warp instructions x 16 pipe cycles over the SMs' cycles: the pipe's busy share"
+    return out
+
+
+def lin_line(N, nnzb, ms, shape, shape_src, hbm_peak):
+    """The linearisation's own figures: cells per second, algorithmic bytes
+    (state in and out, old state, flags, transmissibilities, porosity,
+    residual, Jacobian) against the copy rate, and FP64 instructions
+    against the FP64 pipe's rate (ncu counts stored with their sources)."""
+    alg = 106.0 * N + 72.0 * nnzb
+    traffic = stored("linearize", "dram_bytes")
+    return {"mcells": N / (ms * 1e-3) / 1e6, "ms": ms, "launch_shape": shape, "shape_source": shape_src,
+            "hbm": {"algorithmic_bytes": alg, "bytes_per_cell": alg / N,
+                    "achieved_gbs": alg / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                    "frac": alg / (ms * 1e-3) / 1e9 / hbm_peak if hbm_peak else None,
+                    "traffic": traffic, "traffic_over_algorithmic": traffic / alg if traffic else None},
+            "fp64": fp64_part(stored("linearize", "fp64_inst_per_cell"),
+                              stored("linearize", "fp64_warp_inst_per_cell"), N, ms),
+            "bound": "alu"}
+
+
+def vjp_line(N, nnzb, ms, hbm_peak):
+    """The adjoint product's own figures, as lin_line: algorithmic bytes are
+    the Jacobian, multiplier, face fluxes, ln k weights, both states, flags,
+    porosity and the four gradients."""
+    alg = 72.0 * nnzb + (24 + 72 + 48 + 48 + 2 + 8 + 64) * N
+    traffic = stored("vjp", "dram_bytes")
+    return {"mcells": N / (ms * 1e-3) / 1e6, "ms": ms,
+            "hbm": {"algorithmic_bytes": alg, "bytes_per_cell": alg / N,
+                    "achieved_gbs": alg / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                    "frac": alg / (ms * 1e-3) / 1e9 / hbm_peak if hbm_peak else None,
+                    "traffic": traffic, "traffic_over_algorithmic": traffic / alg if traffic else None},
+            "fp64": fp64_part(stored("vjp", "fp64_inst_per_cell"), stored("vjp", "fp64_warp_inst_per_cell"),
+                              N, ms),
+            "bound": "alu"}
 
 
 def run_ensemble(dev, local_rank, reps=10):
@@ -619,6 +721,27 @@ def run_ensemble(dev, local_rank, reps=10):
     def batched():
         batch.linearize(dt, graph=True)
 
+    # the fairer baseline: each model's three launches captured once as its own
+    # CUDA graph, the 64 graphs replayed back to back (no binding overhead)
+    per_model()
+    torch.cuda.synchronize(dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    model_graphs = []
+    with torch.cuda.stream(side):
+        for grid, io in zip(grids, ios):
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, stream=side):
+                grid.linearize(io["u_new"], io["flag_new"], io["u_old"], io["flag_old"], dt, io["residual"],
+                               io["bsr_val"])
+            model_graphs.append(gr)
+    stream.wait_stream(side)
+    torch.cuda.synchronize(dev)
+
+    def per_model_graphs():
+        for gr in model_graphs:
+            gr.replay()
+
     def timed(fn):
         for _ in range(2):
             fn()
@@ -635,16 +758,32 @@ def run_ensemble(dev, local_rank, reps=10):
 
     t_sep = timed(per_model)
     ref = [(io["residual"].clone(), io["bsr_val"].clone()) for io in ios]
+    t_gr = timed(per_model_graphs)
+    same_gr = all(torch.equal(io["residual"].view(torch.int64), r.view(torch.int64)) and
+                  torch.equal(io["bsr_val"].view(torch.int64), v.view(torch.int64)) for io, (r, v) in zip(ios, ref))
     t_bat = timed(batched)
     same = all(torch.equal(io["residual"].view(torch.int64), r.view(torch.int64)) and
                torch.equal(io["bsr_val"].view(torch.int64), v.view(torch.int64)) for io, (r, v) in zip(ios, ref))
     st = batch.status()
-    return {"workload": "64 black-oil boxes, cell counts log-uniform in 2e4..4e5", "models": len(grids),
-            "cells": ncell, "per_model_ms": t_sep, "batched_graph_ms": t_bat,
-            "per_model_mcells": ncell / (t_sep * 1e-3) / 1e6, "batched_mcells": ncell / (t_bat * 1e-3) / 1e6,
-            "speedup": t_sep / t_bat, "bitwise_equal": bool(same), "device_status": st,
-            "launch_shape": shape, "shape_from_cache": cached, "launches_per_model_path": 3 * len(grids),
-            "launches_batched": 3}
+    out = {"workload": "64 black-oil boxes, cell counts log-uniform in 2e4..4e5", "models": len(grids),
+           "cells": ncell, "per_model_ms": t_sep, "per_model_graphs_ms": t_gr, "batched_graph_ms": t_bat,
+           "per_model_mcells": ncell / (t_sep * 1e-3) / 1e6,
+           "per_model_graphs_mcells": ncell / (t_gr * 1e-3) / 1e6,
+           "batched_mcells": ncell / (t_bat * 1e-3) / 1e6,
+           "speedup": t_sep / t_bat, "speedup_vs_per_model_graphs": t_gr / t_bat,
+           "bitwise_equal": bool(same and same_gr), "device_status": st,
+           "launch_shape": shape, "shape_from_cache": cached, "launches_per_model_path": 3 * len(grids),
+           "launches_batched": 3,
+           "baselines": "per_model: 64 ocp_linearize calls through the binding on one stream; per_model_graphs: "
+                        "each model's three launches captured as its own CUDA graph, 64 replays back to back"}
+    fp = lin_fp64_per_cell()
+    if fp is not None:
+        rate = ncell * fp / (t_bat * 1e-3) / 1e9
+        out["fp64"] = {"inst_per_cell": fp, "achieved_ginst_s": rate, "peak_ginst_s": FP64_NOMINAL_GFLOPS / 2,
+                       "frac": rate / (FP64_NOMINAL_GFLOPS / 2),
+                       "source": "FP64 thread instructions per cell of the three linearisation kernels, ncu "
+                                 "capture of the 100x100x10 box (same kernels as the batch)"}
+    return out
 
 
 def _events(stream):
@@ -670,10 +809,9 @@ def run_small_case(dev, local_rank, reps=200):
     batch = ocp.Batch([grid])
     batch.set_io([io])
     stream = torch.cuda.current_stream(dev)
-    out = {}
-    for name, fn in (("stream_us", lambda: grid.linearize(io["u_new"], io["flag_new"], io["u_old"], io["flag_old"],
-                                                           s.dt, io["residual"], io["bsr_val"])),
-                     ("graph_us", lambda: batch.linearize(s.dt, graph=True))):
+    out = {"default_shape": batch.get_shape()}
+
+    def time_us(fn):
         for _ in range(20):
             fn()
         e0, e1 = _events(stream)
@@ -682,8 +820,17 @@ def run_small_case(dev, local_rank, reps=200):
             fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        out[name] = e0.elapsed_time(e1) * 1e3 / reps
-    out.update(workload="10x10x3 three-phase box (300 cells)", cells=grid.N, status=batch.status())
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    out["stream_us"] = time_us(lambda: grid.linearize(io["u_new"], io["flag_new"], io["u_old"], io["flag_old"],
+                                                      s.dt, io["residual"], io["bsr_val"]))
+    out["graph_us_default_shape"] = time_us(lambda: batch.linearize(s.dt, graph=True))
+    from paper_2406_10862_gb300 import autotune
+    shape, cached = autotune.tuned_shape(batch, s.dt)
+    out["tuned_shape"] = shape
+    out["graph_us"] = time_us(lambda: batch.linearize(s.dt, graph=True))
+    out.update(workload="10x10x3 three-phase box (300 cells)", cells=grid.N, status=batch.status(),
+               graph_us_meaning="one CUDA-graph replay of the linearisation with the autotuned launch shape")
     return out
 
 
@@ -1059,10 +1206,24 @@ def main():
                     help="launch the step's kernels one call at a time instead of replaying per-phase CUDA graphs")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, no CPU baseline): the command profiled by ncu")
+    ap.add_argument("--source-hashes", action="store_true",
+                    help="print the hashes of the kernel sources that the stored ncu figures are keyed to")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch shape of the workload's grid instead of the autotuned one")
+    ap.add_argument("--shape", metavar="JSON",
+                    help="launch shape of the workload's linearisation (the dict of ocp.Grid.set_shape)")
+    ap.add_argument("--box", metavar="NXxNYxNZ",
+                    help="with --profile: run the step on a layered box of this shape instead of 100x100x20 "
+                         "(the small case of an ncu capture)")
     args = ap.parse_args()
+    if args.box and not args.profile:
+        ap.error("--box is only for --profile runs: the benchmark's workload is the 100x100x20 box")
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local_rank = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    if args.source_hashes:
+        print(json.dumps({k: sources_sha16(v["sources"]) for k, v in STORED.items()}))
+        return
     if args.only:
         import torch
         dev = torch.device("cuda", local_rank)
