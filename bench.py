@@ -54,12 +54,15 @@ def env_int(name, default):
 #   dram_bytes          DRAM read + write bytes of one call on the
 #                       100x100x20 workload
 STORED = {
-    "spmv": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": "e67b1c58e0eb034c",
-             "dram_bytes": 105.36e6},
-    "linearize": {"sources": ["linearize.cu", "ocp_internal.cuh"], "sha16": None,
-                  "fp64_inst_per_cell": None, "fp64_warp_inst_per_cell": None, "dram_bytes": None},
-    "vjp": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": None,
-            "fp64_inst_per_cell": None, "fp64_warp_inst_per_cell": None, "dram_bytes": None},
+    "spmv": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": "d309273b7250d8d4",
+             "dram_bytes": 104.515e6, "fp64_inst_per_cell": 63.84, "fp64_warp_inst_per_cell": 2.0041},
+    # DRAM bytes per call by launch mode ("ordered" of the launch shape): 0 with
+    # 128/128/256-cell tiles, 2 with 64-cell tiles
+    "linearize": {"sources": ["linearize.cu", "ocp_internal.cuh"], "sha16": "084e5efeb6879c6b",
+                  "fp64_inst_per_cell": 369.54, "fp64_warp_inst_per_cell": 11.9069,
+                  "dram_bytes": {"0": 323.82e6, "2": 225.14e6}},
+    "vjp": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": "d309273b7250d8d4",
+            "fp64_inst_per_cell": 177.19, "fp64_warp_inst_per_cell": 5.5739, "dram_bytes": 150.81e6},
 }
 
 
@@ -659,7 +662,7 @@ def lin_line(N, nnzb, ms, shape, shape_src, hbm_peak):
     residual, Jacobian) against the copy rate, and FP64 instructions
     against the FP64 pipe's rate (ncu counts stored with their sources)."""
     alg = 106.0 * N + 72.0 * nnzb
-    traffic = stored("linearize", "dram_bytes")
+    traffic = (stored("linearize", "dram_bytes") or {}).get(str(shape["ordered"]))
     return {"mcells": N / (ms * 1e-3) / 1e6, "ms": ms, "launch_shape": shape, "shape_source": shape_src,
             "hbm": {"algorithmic_bytes": alg, "bytes_per_cell": alg / N,
                     "achieved_gbs": alg / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
@@ -828,9 +831,15 @@ def run_small_case(dev, local_rank, reps=200):
     from paper_2406_10862_gb300 import autotune
     shape, cached = autotune.tuned_shape(batch, s.dt)
     out["tuned_shape"] = shape
-    out["graph_us"] = time_us(lambda: batch.linearize(s.dt, graph=True))
+    out["graph_us_tuned_shape"] = time_us(lambda: batch.linearize(s.dt, graph=True))
+    # the tuner times stream launches, whose launch overhead favours fewer
+    # launches; under graph replay either shape may win, so both are timed
+    best = min(("default_shape", out["graph_us_default_shape"]), ("tuned_shape", out["graph_us_tuned_shape"]),
+               key=lambda t: t[1])
+    out["graph_us"] = best[1]
     out.update(workload="10x10x3 three-phase box (300 cells)", cells=grid.N, status=batch.status(),
-               graph_us_meaning="one CUDA-graph replay of the linearisation with the autotuned launch shape")
+               graph_us_meaning="one CUDA-graph replay of the linearisation, the faster of the default and the "
+                                "autotuned launch shape (%s)" % best[0])
     return out
 
 
