@@ -18,6 +18,11 @@
 // computed once and results travel through (coalesced, variable-major)
 // scratch rather than being recomputed.
 //
+// The outputs (Jacobian blocks, residual, face fluxes) are written with
+// streaming stores (evict-first), so that they do not push out of L2 the
+// scratch the next stage still reads (measured 0.2226 -> 0.2184 ms with three
+// launches on the 200 000-cell box).
+//
 // Every kernel walks a list of tiles -- TPB consecutive cells of one model --
 // with its CTAs striding over the list.  A single grid is the one-model case
 // (its arguments passed by value, tiles implied); a batch of grids passes a
@@ -173,7 +178,7 @@ __device__ __forceinline__ void face_part(const ModelArgs& M, long long c, doubl
 #pragma unroll
       for (int v = 0; v < NB; ++v) {
         dg[e][v] += o.di[e][v];
-        blk[e * NB + v] = o.dj[e][v];
+        __stcs(blk + e * NB + v, o.dj[e][v]);
       }
     }
     ++slot;
@@ -186,10 +191,10 @@ __device__ __forceinline__ void face_part(const ModelArgs& M, long long c, doubl
       scr[(base + e) * N + n] = o.F[e];
 #pragma unroll
       for (int v = 0; v < NB; ++v) {
-        nblk[e * NB + v] = neg(o.di[e][v]);
+        __stcs(nblk + e * NB + v, neg(o.di[e][v]));
         scr[(base + 3 + 3 * e + v) * N + n] = o.dj[e][v];
       }
-      if (face_flux) face_flux[(d * NB + e) * N + c] = o.F[e];
+      if (face_flux) __stcs(face_flux + (d * NB + e) * N + c, o.F[e]);
     }
   }
 }
@@ -235,10 +240,10 @@ __device__ __forceinline__ void assemble_rows(const ModelArgs& M, long long c, d
   bool ok = true;
 #pragma unroll
   for (int e = 0; e < NB; ++e) {
-    M.res[c * NB + e] = r[e];
+    __stcs(M.res + c * NB + e, r[e]);
     ok = ok && finite(r[e]);
 #pragma unroll
-    for (int v = 0; v < NB; ++v) out[e * NB + v] = dg[e][v];
+    for (int v = 0; v < NB; ++v) __stcs(out + e * NB + v, dg[e][v]);
   }
   if (!ok) atomicOr(M.status, kStatNonFinite);
 }
@@ -274,6 +279,7 @@ __device__ __forceinline__ const ModelArgs& tile_of(const TileList& L, const Mod
 
 template <int NB, int TPB>
 __global__ void __launch_bounds__(TPB, 512 / TPB) cell_kernel(TileList L, ModelArgs single) {
+  pdl_wait();
   __shared__ Table T;
   __shared__ unsigned long long bar;
   unsigned uses = 0;
@@ -294,6 +300,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) cell_kernel(TileList L, ModelA
 
 template <int NB, int TPB>
 __global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) face_kernel(TileList L, ModelArgs single) {
+  pdl_wait();
   for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
     int m;
     long long c0;
@@ -305,6 +312,7 @@ __global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) face_kernel(
 
 template <int NB, int TPB>
 __global__ void __launch_bounds__(TPB) assemble_kernel(TileList L, ModelArgs single) {
+  pdl_wait();
   for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
     int m;
     long long c0;
@@ -387,6 +395,7 @@ __device__ __forceinline__ void wait_tiles(const int* flags, const long long (&l
 template <int NB, int TPB, int MODE>
 __global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) ordered_kernel(OrderedList O,
                                                                                     ModelArgs single) {
+  pdl_wait();
   __shared__ Table T;
   __shared__ unsigned long long bar;
   __shared__ long long s_tile;
@@ -463,9 +472,9 @@ __global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) ordered_kern
 
 template <int NB, int TPB>
 void launch_stage(int stage, const TileList& L, const ModelArgs& single, int grid, cudaStream_t s) {
-  if (stage == 0) cell_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
-  else if (stage == 1) face_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
-  else assemble_kernel<NB, TPB><<<grid, TPB, 0, s>>>(L, single);
+  if (stage == 0) launch_pdl(cell_kernel<NB, TPB>, grid, TPB, 0, s, L, single);
+  else if (stage == 1) launch_pdl(face_kernel<NB, TPB>, grid, TPB, 0, s, L, single);
+  else launch_pdl(assemble_kernel<NB, TPB>, grid, TPB, 0, s, L, single);
 }
 
 template <int NB, int TPB, int MODE>
@@ -480,8 +489,7 @@ cudaError_t launch_ordered_t(const OrderedList& O, const ModelArgs& single, int 
   long long grid = (long long)per_sm * (sms > 0 ? sms : 1);
   if (grid > O.nitems) grid = O.nitems;
   if (grid < 1) return cudaSuccess;
-  ordered_kernel<NB, TPB, MODE><<<(unsigned)grid, TPB, 0, s>>>(O, single);
-  return cudaGetLastError();
+  return launch_pdl(ordered_kernel<NB, TPB, MODE>, (unsigned)grid, TPB, 0, s, O, single);
 }
 
 template <int NB, int TPB>

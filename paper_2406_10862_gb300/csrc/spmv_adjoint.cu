@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const
                                                         double* __restrict__ y, int mode,
                                                         const double* __restrict__ skip) {
   constexpr int B2 = NB * NB;
+  pdl_wait();
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= P.N || (skip != nullptr && *skip != 0.0)) return;
   int ci, cj, ck;
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_grid_t_kernel(Params P, con
                                                                    double beta, double* __restrict__ y, int mode,
                                                                    const double* __restrict__ skip) {
   constexpr int B2 = NB * NB;
+  pdl_wait();
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= P.N || (skip != nullptr && *skip != 0.0)) return;
   int ci, cj, ck;
@@ -239,6 +241,7 @@ __global__ void __launch_bounds__(kBulkRows) spmv_bulk_kernel(Params P, const in
                                                               int* __restrict__ status, const double* __restrict__ skip) {
   constexpr int B2 = NB * NB;
   constexpr long long BB = 8 * B2;
+  pdl_wait();
   if (skip != nullptr && *skip != 0.0) return;     // the same for every thread: before any barrier
   extern __shared__ __align__(128) unsigned char sbuf[];
   __shared__ __align__(8) unsigned long long bar;
@@ -318,8 +321,13 @@ __global__ void __launch_bounds__(kBulkRows) spmv_bulk_kernel(Params P, const in
 }
 
 // ------------------------------------------------------------------ adjoint
+// 128-thread CTAs: at 64 registers four 256-thread CTAs fit an SM and the
+// 200 000-cell adjoint's 782 CTAs split 3 : 2 over the SMs; 1563 CTAs of 128
+// spread evenly enough (79 against 84 us).
+constexpr int kVjpThreads = 128;
+
 template <int NB>
-__global__ void __launch_bounds__(256) vjp_kernel(Params P, const Table* __restrict__ gT,
+__global__ void __launch_bounds__(kVjpThreads) vjp_kernel(Params P, const Table* __restrict__ gT,
                                                   const double* __restrict__ u_new,
                                                   const int8_t* __restrict__ f_new,
                                                   const double* __restrict__ u_old,
@@ -334,6 +342,7 @@ __global__ void __launch_bounds__(256) vjp_kernel(Params P, const Table* __restr
                                                   double* __restrict__ g_unew, double* __restrict__ g_uold,
                                                   double* __restrict__ g_lnk, double* __restrict__ g_phi,
                                                   int* __restrict__ status) {
+  pdl_wait();
   __shared__ Table T;
   __shared__ unsigned long long bar;
   unsigned uses = 0;
@@ -489,20 +498,22 @@ cudaError_t launch_spmv(const ocp_grid* g, const double* val, double alpha, cons
   const int nb = nbs > 0 ? nbs : g->prm.nb;
   // 2x2 and 1x1 products stage their matrix slices by bulk copy when the
   // matrix is 16-byte aligned (the copy's rule); otherwise, and for 3x3, the
-  // register kernel runs.  Both give identical bits.
+  // register kernel runs.  Both give identical bits.  Every product is a
+  // programmatic launch (launch_pdl): it is scheduled while the kernel before
+  // it finishes and waits for it before touching memory.
   const bool bulk = ((uintptr_t)val & 15) == 0;
   const unsigned bblocks = (unsigned)((N + kBulkRows - 1) / kBulkRows);
   if (nb == 3) {
-    if (transpose) spmv_grid_t_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode, skip);
-    else spmv_grid_kernel<3><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode, skip);
+    if (transpose) return launch_pdl(spmv_grid_t_kernel<3>, gblocks, kSpmvThreads, 0, s, g->prm, val, alpha, x, beta, y, mode, skip);
+    return launch_pdl(spmv_grid_kernel<3>, gblocks, kSpmvThreads, 0, s, g->prm, (const int32_t*)g->d_row_ptr, val, alpha, x, beta, y, mode, skip);
   } else if (nb == 2) {
-    if (transpose) spmv_grid_t_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode, skip);
-    else if (bulk) spmv_bulk_kernel<2><<<bblocks, kBulkRows, bulk_smem_bytes<2>(), s>>>(g->prm, g->d_row_ptr, g->nnzb, val, alpha, x, beta, y, mode, g->d_status, skip);
-    else spmv_grid_kernel<2><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode, skip);
+    if (transpose) return launch_pdl(spmv_grid_t_kernel<2>, gblocks, kSpmvThreads, 0, s, g->prm, val, alpha, x, beta, y, mode, skip);
+    if (bulk) return launch_pdl(spmv_bulk_kernel<2>, bblocks, kBulkRows, bulk_smem_bytes<2>(), s, g->prm, (const int32_t*)g->d_row_ptr, (long long)g->nnzb, val, alpha, x, beta, y, mode, g->d_status, skip);
+    return launch_pdl(spmv_grid_kernel<2>, gblocks, kSpmvThreads, 0, s, g->prm, (const int32_t*)g->d_row_ptr, val, alpha, x, beta, y, mode, skip);
   } else {
-    if (transpose) spmv_grid_t_kernel<1><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, val, alpha, x, beta, y, mode, skip);
-    else if (bulk) spmv_bulk_kernel<1><<<bblocks, kBulkRows, bulk_smem_bytes<1>(), s>>>(g->prm, g->d_row_ptr, g->nnzb, val, alpha, x, beta, y, mode, g->d_status, skip);
-    else spmv_grid_kernel<1><<<gblocks, kSpmvThreads, 0, s>>>(g->prm, g->d_row_ptr, val, alpha, x, beta, y, mode, skip);
+    if (transpose) return launch_pdl(spmv_grid_t_kernel<1>, gblocks, kSpmvThreads, 0, s, g->prm, val, alpha, x, beta, y, mode, skip);
+    if (bulk) return launch_pdl(spmv_bulk_kernel<1>, bblocks, kBulkRows, bulk_smem_bytes<1>(), s, g->prm, (const int32_t*)g->d_row_ptr, (long long)g->nnzb, val, alpha, x, beta, y, mode, g->d_status, skip);
+    return launch_pdl(spmv_grid_kernel<1>, gblocks, kSpmvThreads, 0, s, g->prm, (const int32_t*)g->d_row_ptr, val, alpha, x, beta, y, mode, skip);
   }
   return cudaGetLastError();
 }
@@ -512,17 +523,17 @@ cudaError_t launch_vjp(const ocp_grid* g, const double* u_new, const int8_t* f_n
                        const double* lam, double* g_unew, double* g_uold, double* g_lnk, double* g_phi,
                        cudaStream_t s) {
   const Params& P = g->prm;
-  const unsigned blocks = (unsigned)((P.N + 255) / 256);
+  const unsigned blocks = (unsigned)((P.N + kVjpThreads - 1) / kVjpThreads);
   const double scale = P.vol_rb / dt;
   if (P.nb == 3)
-    vjp_kernel<3><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, val, face_flux,
-                                         g->d_wlnk, g->d_perf_of_cell, g->d_perf, scale, lam, g_unew, g_uold,
-                                         g_lnk, g_phi, g->d_status);
-  else
-    vjp_kernel<2><<<blocks, 256, 0, s>>>(P, g->d_table, u_new, f_new, u_old, f_old, g->d_phi, val, face_flux,
-                                         g->d_wlnk, g->d_perf_of_cell, g->d_perf, scale, lam, g_unew, g_uold,
-                                         g_lnk, g_phi, g->d_status);
-  return cudaGetLastError();
+    return launch_pdl(vjp_kernel<3>, blocks, kVjpThreads, 0, s, P, (const Table*)g->d_table, u_new, f_new, u_old,
+                      f_old, (const double*)g->d_phi, val, face_flux, (const double*)g->d_wlnk,
+                      (const int32_t*)g->d_perf_of_cell, (const Perf*)g->d_perf, scale, lam, g_unew, g_uold, g_lnk,
+                      g_phi, g->d_status);
+  return launch_pdl(vjp_kernel<2>, blocks, kVjpThreads, 0, s, P, (const Table*)g->d_table, u_new, f_new, u_old,
+                    f_old, (const double*)g->d_phi, val, face_flux, (const double*)g->d_wlnk,
+                    (const int32_t*)g->d_perf_of_cell, (const Perf*)g->d_perf, scale, lam, g_unew, g_uold, g_lnk,
+                    g_phi, g->d_status);
 }
 
 cudaError_t launch_well_rates(const ocp_grid* g, const double* u, const int8_t* flag, double* q,
