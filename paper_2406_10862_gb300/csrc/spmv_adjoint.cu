@@ -88,12 +88,15 @@ __global__ void setup_kernel(Params P, const double* __restrict__ lnk, double dx
 // and the row's first block from the closed form of the row pointer (no
 // dependent index loads), all x entries of the row are loaded first, then
 // each block is loaded and consumed.  Rows with missing neighbours read x
-// at their own cell instead and skip those blocks.  128-thread CTAs measured
-// fastest (28.4 us against 30.3 us with 256 at 200 000 rows).
-constexpr int kSpmvThreads = 128;
+// at their own cell instead and skip those blocks.  One-warp CTAs with a
+// budget of 80 registers (24 warps per SM) measured fastest at 200 000 rows:
+// 25.3 us against 25.8 us for 128-thread CTAs at 64 registers (32 warps),
+// 25.4 for 64-thread CTAs at 80; 96 registers (20 warps) 26.5 us.
+constexpr int kSpmvThreads = 32;
+constexpr int kSpmvMinBlocks = 24;
 
 template <int NB>
-__global__ void __launch_bounds__(kSpmvThreads) spmv_grid_kernel(Params P, const int32_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(kSpmvThreads, kSpmvMinBlocks) spmv_grid_kernel(Params P, const int32_t* __restrict__ row_ptr,
                                                         const double* __restrict__ val, double alpha,
                                                         const double* __restrict__ x, double beta,
                                                         double* __restrict__ y, int mode,
