@@ -221,7 +221,10 @@ typedef struct {
  * SM, 0: as many as fit).  ordered = 2: one persistent launch of both the
  * cell and the face stages, each tile's cell stage claimed ahead of the face
  * stages that need it.  The waits on other tiles are bounded: one that
- * expires makes ocp_get_status return OCP_ERR_TIMEOUT.
+ * expires makes ocp_get_status return OCP_ERR_TIMEOUT.  ordered = 3: three
+ * launches, the face stage with one warp per direction and the assembly with
+ * one warp per equation over 32-cell tiles (cell stage as set), which
+ * shortens each warp's chain of FP64 instructions for small grids.
  * Results do not depend on the shape, bit for bit. */
 typedef struct {
   int cells_per_tile[3];
@@ -265,7 +268,8 @@ ocp_status ocp_batch_get_status(ocp_batch* batch, void* cuda_stream);
  * ocp_batch_tune on a batch of that grid alone).  A new grid starts with one
  * CTA per tile and the largest tiles (128 cells for the cell and face stages,
  * 256 for assembly) that still give every SM two CTAs, halving down to 32
- * cells for small grids. */
+ * cells for small grids; grids of fewer than 64 cells per SM start with
+ * ordered = 3. */
 ocp_status ocp_grid_set_shape(ocp_grid* grid, const ocp_launch_shape* shape);
 /* The launch shape ocp_linearize currently uses on the grid. */
 ocp_status ocp_grid_get_shape(const ocp_grid* grid, ocp_launch_shape* shape);

@@ -96,7 +96,7 @@ cudaError_t run_cfg(ocp_batch* b, const ocp::LaunchCfg& cfg, cudaStream_t s) {
   ocp::TileList L[ocp::kNumTileSizes];
   lists_of(b, L);
   ocp::ModelArgs unused{};
-  if (cfg.ordered == 0) return ocp::launch_tiles(b->nb, L, unused, cfg, b->sms, s);
+  if (cfg.ordered == 0 || cfg.ordered == 3) return ocp::launch_tiles(b->nb, L, unused, cfg, b->sms, s);
   const int ti = ocp::tile_index(cfg.tpb[1]);
   if (ti < 0) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned) * (1 + 2 * b->nsync_tiles), s);
@@ -123,7 +123,7 @@ ocp_status check_shape(const ocp_launch_shape* sh) {
     if (sh->ctas_per_sm[s] < 0 || sh->ctas_per_sm[s] > 64)
       return ocp::report(OCP_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
   }
-  if (sh->ordered < 0 || sh->ordered > 2) return ocp::report(OCP_ERR_INVALID_ARG, "ordered must be 0, 1 or 2");
+  if (sh->ordered < 0 || sh->ordered > 3) return ocp::report(OCP_ERR_INVALID_ARG, "ordered must be 0, 1, 2 or 3");
   return OCP_OK;
 }
 
@@ -362,6 +362,17 @@ ocp_status ocp_batch_tune(ocp_batch* b, double dt, int reps, ocp_launch_shape* b
     time_pass(cur, best_ms);
     const int octas[4] = {0, 1, 2, 4};
     ocp::LaunchCfg base = cur;
+    {                                   // the split face and assembly stages
+      ocp::LaunchCfg c = base;
+      c.ordered = 3;
+      c.ctas_per_sm[1] = c.ctas_per_sm[2] = 0;
+      float ms = 1e30f;
+      time_pass(c, ms);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        cur = c;
+      }
+    }
     for (int mode = 1; mode <= 2 && e == cudaSuccess; ++mode)
       for (int ti = 0; ti < ocp::kNumTileSizes && e == cudaSuccess; ++ti)
         for (int ci = 0; ci < 4 && e == cudaSuccess; ++ci) {

@@ -322,6 +322,135 @@ __global__ void __launch_bounds__(TPB) assemble_kernel(TileList L, ModelArgs sin
   }
 }
 
+// -------------------------------------------------- split face and assembly
+// For small grids, whose time is the FP64 instruction count of their warps
+// (each FP64 warp instruction holds a sub-partition's FP64 unit 64 cycles):
+// the face stage with one warp per direction and the assembly with one warp
+// per equation, over 32-cell tiles, so that a warp does a third of a cell's
+// work.  Same arithmetic in the same order as face_kernel and
+// assemble_kernel: bit-identical results.
+
+// Face d of cell c: the blocks and the + neighbour's share as in face_part;
+// this row's own terms (F, dF/du_c) go to own[0..12)[lane] for the combine.
+template <int NB>
+__device__ __forceinline__ void face_dir(const ModelArgs& M, long long c, int d, double (*own)[32], int lane) {
+  constexpr int B2 = NB * NB;
+  const Params& P = M.P;
+  const long long N = P.N;
+  double* scr = M.scr;
+  double* __restrict__ face_flux = M.face_flux;
+  int i, j, k;
+  cell_ijk(P, c, i, j, k);
+  const bool hm[3] = {i > 0, j > 0, k > 0};
+  const bool hp[3] = {i + 1 < P.nx, j + 1 < P.ny, k + 1 < P.nz};
+  if (!hp[d]) {
+    if (face_flux)
+      for (int e = 0; e < NB; ++e) __stcs(face_flux + (d * NB + e) * N + c, 0.0);
+    return;
+  }
+  const long long stride = d == 0 ? 1 : (d == 1 ? (long long)P.nx : P.nxy);
+  const long long n = c + stride;
+  CellQ a, b;
+  load_q<NB>(scr, N, c, a);
+  load_q<NB>(scr, N, n, b);
+  FaceOut<NB> o;
+  const double T = M.trans[d * N + c];
+  if (d == 2) face_terms<NB, true>(T, -P.grav_dz, a, b, o);
+  else face_terms<NB, false>(T, 0.0, a, b, o);
+  const int slot = (int)hm[0] + (int)hm[1] + (int)hm[2] + 1 + (d > 0 && hp[0]) + (d > 1 && hp[1]);
+  double* blk = M.val + (row_start_ijk(P, c, i, j, k) + slot) * B2;
+  const int slot_n = (d == 0) ? ((int)hm[2] + (int)hm[1]) : (d == 1 ? (int)hm[2] : 0);
+  double* nblk = M.val + (row_start_ijk(P, n, i + (d == 0), j + (d == 1), k + (d == 2)) + slot_n) * B2;
+  const int base = kInc + 12 * d;
+#pragma unroll
+  for (int e = 0; e < NB; ++e) {
+    own[e][lane] = o.F[e];
+    scr[(base + e) * N + n] = o.F[e];
+#pragma unroll
+    for (int v = 0; v < NB; ++v) {
+      own[3 + 3 * e + v][lane] = o.di[e][v];
+      __stcs(blk + e * NB + v, o.dj[e][v]);
+      __stcs(nblk + e * NB + v, neg(o.di[e][v]));
+      scr[(base + 3 + 3 * e + v) * N + n] = o.dj[e][v];
+    }
+    if (face_flux) __stcs(face_flux + (d * NB + e) * N + c, o.F[e]);
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(96) face_split_kernel(TileList L, ModelArgs single) {
+  pdl_wait();
+  __shared__ double own[3][12][32];      // [direction][F, dF/du_c][lane]
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
+    int m;
+    long long c0;
+    const ModelArgs& M = tile_of<32>(L, single, t, m, c0);
+    const long long N = M.P.N;
+    const long long c = c0 + lane;
+    if (c < N) face_dir<NB>(M, c, w, own[w], lane);
+    __syncthreads();
+    if (c < N && w < NB) {               // warp e: equation e of this row, own terms + faces x, y, z
+      int i, j, k;
+      cell_ijk(M.P, c, i, j, k);
+      const bool hp[3] = {i + 1 < M.P.nx, j + 1 < M.P.ny, k + 1 < M.P.nz};
+      double* scr = M.scr;
+      const int e = w;
+      double r = scr[(kSelf + e) * N + c];
+      double dg[NB];
+#pragma unroll
+      for (int v = 0; v < NB; ++v) dg[v] = scr[(kSelf + 3 + 3 * e + v) * N + c];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (!hp[d]) continue;
+        r += own[d][e][lane];
+#pragma unroll
+        for (int v = 0; v < NB; ++v) dg[v] += own[d][3 + 3 * e + v][lane];
+      }
+      scr[(kPart + e) * N + c] = r;
+#pragma unroll
+      for (int v = 0; v < NB; ++v) scr[(kPart + 3 + 3 * e + v) * N + c] = dg[v];
+    }
+    __syncthreads();                     // own[] is reused by the next tile
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(96) assemble_split_kernel(TileList L, ModelArgs single) {
+  pdl_wait();
+  const int e = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (e >= NB) return;
+  for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
+    int m;
+    long long c0;
+    const ModelArgs& M = tile_of<32>(L, single, t, m, c0);
+    const long long N = M.P.N;
+    const long long c = c0 + lane;
+    if (c >= N) continue;
+    const double* scr = M.scr;
+    int i, j, k;
+    cell_ijk(M.P, c, i, j, k);
+    const bool hm[3] = {i > 0, j > 0, k > 0};
+    double r = scr[(kPart + e) * N + c];
+    double dg[NB];
+#pragma unroll
+    for (int v = 0; v < NB; ++v) dg[v] = scr[(kPart + 3 + 3 * e + v) * N + c];
+#pragma unroll
+    for (int d = 2; d >= 0; --d) {
+      if (!hm[d]) continue;
+      const int base = kInc + 12 * d;
+      r -= scr[(base + e) * N + c];
+#pragma unroll
+      for (int v = 0; v < NB; ++v) dg[v] -= scr[(base + 3 + 3 * e + v) * N + c];
+    }
+    double* out = M.val + (row_start_ijk(M.P, c, i, j, k) + (int)hm[0] + (int)hm[1] + (int)hm[2]) * NB * NB;
+    __stcs(M.res + c * NB + e, r);
+#pragma unroll
+    for (int v = 0; v < NB; ++v) __stcs(out + e * NB + v, dg[v]);
+    if (!finite(r)) atomicOr(M.status, kStatNonFinite);
+  }
+}
+
 // ------------------------------------------------------------ ordered launch
 // One persistent launch whose CTAs claim work items in a fixed global order
 // from a device counter.  An item is the cell stage or the face-and-assembly
@@ -541,6 +670,19 @@ cudaError_t launch_tiles(int nb, const TileList* lists, const ModelArgs& single,
                          int sms, cudaStream_t s) {
   for (int stage = 0; stage < 3; ++stage) {
     if (cfg.ctas_per_sm[stage] < 0) continue;
+    if (cfg.ordered == 3 && stage > 0) {   // the split face and assembly stages, 32-cell tiles
+      const TileList& L = lists[0];
+      if (L.ntiles == 0) continue;
+      int grid = cfg.ctas_per_sm[stage] > 0 ? cfg.ctas_per_sm[stage] * sms : L.ntiles;
+      if (grid > L.ntiles) grid = L.ntiles;
+      cudaError_t e;
+      if (nb == 3) e = stage == 1 ? launch_pdl(face_split_kernel<3>, grid, 96, 0, s, L, single)
+                                  : launch_pdl(assemble_split_kernel<3>, grid, 96, 0, s, L, single);
+      else e = stage == 1 ? launch_pdl(face_split_kernel<2>, grid, 96, 0, s, L, single)
+                          : launch_pdl(assemble_split_kernel<2>, grid, 96, 0, s, L, single);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     const int t = tile_index(cfg.tpb[stage]);
     if (t < 0) return cudaErrorInvalidValue;
     const TileList& L = lists[t];
@@ -604,7 +746,7 @@ cudaError_t launch_single(const ocp_grid* g, double* scratch, const double* u_ne
     lists[t].tiles = nullptr;
     lists[t].ntiles = (int)((g->prm.N + kTileSizes[t] - 1) / kTileSizes[t]);
   }
-  if (g->cfg.ordered == 0) return launch_tiles(g->prm.nb, lists, M, g->cfg, g->sms, s);
+  if (g->cfg.ordered == 0 || g->cfg.ordered == 3) return launch_tiles(g->prm.nb, lists, M, g->cfg, g->sms, s);
   const long long nmax = (g->prm.N + 31) / 32;       // flags sized for the smallest tiles
   cudaError_t e = cudaMemsetAsync(g->d_sync, 0, sizeof(unsigned) * (1 + 2 * nmax), s);
   if (e != cudaSuccess) return e;
@@ -629,8 +771,12 @@ cudaError_t preload_linearize(int nb) {
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, ordered_kernel<NB, TPB, 2>);
   if (nb == 3) {
     OCP_LOAD(3, 32) OCP_LOAD(3, 64) OCP_LOAD(3, 128) OCP_LOAD(3, 256)
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, face_split_kernel<3>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, assemble_split_kernel<3>);
   } else {
     OCP_LOAD(2, 32) OCP_LOAD(2, 64) OCP_LOAD(2, 128) OCP_LOAD(2, 256)
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, face_split_kernel<2>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, assemble_split_kernel<2>);
   }
 #undef OCP_LOAD
   return e;

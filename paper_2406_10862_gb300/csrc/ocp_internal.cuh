@@ -80,7 +80,8 @@ struct LaunchCfg {
   int tpb[3];
   int ctas_per_sm[3];
   int ordered;     // 0: three launches; 1: cell launch + ordered face/assembly launch
-                   // (tile size tpb[1], grid ctas_per_sm[1]); 2: one ordered launch
+                   // (tile size tpb[1], grid ctas_per_sm[1]); 2: one ordered launch;
+                   // 3: three launches, face and assembly split by direction / equation
 };
 constexpr int kNumTileSizes = 4;
 constexpr int kTileSizes[kNumTileSizes] = {32, 64, 128, 256};
@@ -92,17 +93,19 @@ inline int tile_index(int tpb) {
 // Default launch shape of one grid of N cells on an SM count `sms`: the
 // largest tiles (128 for the register-heavy cell and face stages, 256 for
 // assembly) that still give every SM at least two CTAs, down to 32-cell
-// tiles, so that a small grid spreads its FP64 work over many SMs instead of
-// a few.
+// tiles; a grid too small for that (fewer than 64 cells per SM) takes the
+// face stage split by direction and the assembly by equation, since its
+// time is its warps' FP64 instruction count, not the SMs' throughput.
 inline LaunchCfg default_cfg(long long N, int sms) {
   LaunchCfg c;
+  const long long S = sms > 0 ? sms : 1;
   for (int s = 0; s < 3; ++s) {
     int t = s < 2 ? 128 : 256;
-    while (t > 32 && N < 2LL * t * (sms > 0 ? sms : 1)) t /= 2;
+    while (t > 32 && N < 2LL * t * S) t /= 2;
     c.tpb[s] = t;
     c.ctas_per_sm[s] = 0;
   }
-  c.ordered = 0;
+  c.ordered = N < 2LL * 32 * S ? 3 : 0;
   return c;
 }
 

@@ -61,7 +61,9 @@ def test_batch_equals_per_model_bitwise_for_every_shape(nphase):
               dict(cells_per_tile=[64, 32, 256], ctas_per_sm=[2, 1, 0], ordered=1),
               dict(cells_per_tile=[128, 128, 256], ctas_per_sm=[0, 0, 0], ordered=2),
               dict(cells_per_tile=[128, 256, 128], ctas_per_sm=[0, 1, 0], ordered=2),
-              dict(cells_per_tile=[128, 32, 128], ctas_per_sm=[0, 2, 0], ordered=2)]
+              dict(cells_per_tile=[128, 32, 128], ctas_per_sm=[0, 2, 0], ordered=2),
+              dict(cells_per_tile=[64, 32, 32], ctas_per_sm=[0, 0, 0], ordered=3),
+              dict(cells_per_tile=[32, 32, 32], ctas_per_sm=[1, 2, 1], ordered=3)]
     for k, sh in enumerate(shapes):
         batch.set_shape(sh)
         for io in ios:
@@ -109,7 +111,7 @@ def test_tuner_returns_a_valid_shape_and_keeps_results():
     batch.set_io(ios)
     best = batch.tune(1.0, reps=2)
     assert all(t in (32, 64, 128, 256) for t in best["cells_per_tile"])
-    assert all(0 <= c <= 16 for c in best["ctas_per_sm"]) and best["ordered"] in (0, 1, 2)
+    assert all(0 <= c <= 16 for c in best["ctas_per_sm"]) and best["ordered"] in (0, 1, 2, 3)
     assert batch.get_shape() == best
     batch.linearize(1.0, graph=True)
     torch.cuda.synchronize()
@@ -134,4 +136,4 @@ def test_batch_status_and_errors():
     with pytest.raises(O.OcpError):
         batch.set_shape(dict(cells_per_tile=[48, 256, 256], ctas_per_sm=[0, 0, 0]))
     with pytest.raises(O.OcpError):
-        batch.set_shape(dict(cells_per_tile=[64, 256, 256], ctas_per_sm=[0, 0, 0], ordered=3))
+        batch.set_shape(dict(cells_per_tile=[64, 256, 256], ctas_per_sm=[0, 0, 0], ordered=4))

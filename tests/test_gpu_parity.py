@@ -93,7 +93,8 @@ def test_launch_shapes_are_bitwise_identical(nphase, shape):
     """Every launch shape of one grid -- tile sizes 32 to 256, one CTA per
     tile or persistent grids, three launches or the ordered launches (face
     stage and assembly in one persistent launch after the cell stage, or
-    everything in one) -- gives the same bits, and those match the oracle."""
+    everything in one), or faces and assembly split by direction and equation
+    -- gives the same bits, and those match the oracle."""
     O = ocp()
     g, s = W.tiny(*shape, nphase=nphase, seed=sum(shape) + 7, frac_unsat=0.3 if nphase == 3 else 0.0)
     grid = O.Grid(g)
@@ -108,6 +109,9 @@ def test_launch_shapes_are_bitwise_identical(nphase, shape):
         for t in (32, 64, 128, 256):
             shapes.append(dict(cells_per_tile=[t, t, 256], ctas_per_sm=[0, 0, 0], ordered=mode))
         shapes.append(dict(cells_per_tile=[64, 128, 256], ctas_per_sm=[0, 1, 0], ordered=mode))
+    # face and assembly split by direction and equation
+    shapes.append(dict(cells_per_tile=[32, 32, 32], ctas_per_sm=[0, 0, 0], ordered=3))
+    shapes.append(dict(cells_per_tile=[128, 32, 32], ctas_per_sm=[2, 1, 3], ordered=3))
     for sh in shapes:
         grid.set_shape(sh)
         got = gpu_linearize(grid, s)
