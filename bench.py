@@ -54,15 +54,15 @@ def env_int(name, default):
 #   dram_bytes          DRAM read + write bytes of one call on the
 #                       100x100x20 workload
 STORED = {
-    "spmv": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": "d309273b7250d8d4",
-             "dram_bytes": 104.515e6, "fp64_inst_per_cell": 63.84, "fp64_warp_inst_per_cell": 2.0041},
+    "spmv": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": "58cb333ed849cc83",
+             "dram_bytes": 104.01e6, "fp64_inst_per_cell": 63.84, "fp64_warp_inst_per_cell": 2.0041},
     # DRAM bytes per call by launch mode ("ordered" of the launch shape): 0 with
     # 128/128/256-cell tiles, 2 with 64-cell tiles
-    "linearize": {"sources": ["linearize.cu", "ocp_internal.cuh"], "sha16": "084e5efeb6879c6b",
+    "linearize": {"sources": ["linearize.cu", "ocp_internal.cuh"], "sha16": "b888eeeffa1aa3ea",
                   "fp64_inst_per_cell": 369.54, "fp64_warp_inst_per_cell": 11.9069,
-                  "dram_bytes": {"0": 323.82e6, "2": 225.14e6}},
-    "vjp": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": "d309273b7250d8d4",
-            "fp64_inst_per_cell": 177.19, "fp64_warp_inst_per_cell": 5.5739, "dram_bytes": 150.81e6},
+                  "dram_bytes": {"0": 326.52e6, "2": 218.13e6}},
+    "vjp": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": "58cb333ed849cc83",
+            "fp64_inst_per_cell": 177.19, "fp64_warp_inst_per_cell": 5.5739, "dram_bytes": 147.50e6},
 }
 
 
