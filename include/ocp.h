@@ -225,6 +225,12 @@ typedef struct {
  * launches, the face stage with one warp per direction and the assembly with
  * one warp per equation over 32-cell tiles (cell stage as set), which
  * shortens each warp's chain of FP64 instructions for small grids.
+ * ordered = 4: the stages of ordered = 3 (cell stage on 32-cell tiles) in
+ * one launch of one thread-block cluster, one CTA per 32-cell tile, the
+ * stages separated by cluster barriers instead of launch boundaries; only
+ * for a single grid (or a batch of one) of at most ocp_grid_cluster_tiles
+ * tiles, other shapes being rejected with OCP_ERR_INVALID_ARG when set.
+ * The tile sizes and CTA counts are ignored in this mode.
  * Results do not depend on the shape, bit for bit. */
 typedef struct {
   int cells_per_tile[3];
@@ -252,10 +258,12 @@ ocp_status ocp_batch_linearize(ocp_batch* batch, double dt, void* cuda_stream);
  * a private stream) into a CUDA graph that is replayed on cuda_stream. */
 ocp_status ocp_batch_graph_launch(ocp_batch* batch, double dt, void* cuda_stream);
 
-/* Autotuner: times every stage with 4 tile sizes x 6 grid sizes (median of
- * reps after a warm-up) and keeps the fastest per stage, then times the whole
- * pass so found against the ordered launches (modes 1 and 2, 4 tile sizes,
- * 4 grid sizes) and keeps the fastest; returns it in *best (may be NULL).
+/* Autotuner: times every stage as a plain launch (ordered = 0) with 4 tile
+ * sizes x 6 grid sizes (median of reps after a warm-up) and keeps the
+ * fastest per stage, then times the whole pass so found against the split
+ * stages (ordered = 3, and ordered = 4 when the batch is one grid that fits
+ * one cluster) and the ordered launches (modes 1 and 2, 4 tile sizes, 4 grid
+ * sizes) and keeps the fastest; returns it in *best (may be NULL).
  * Synchronises the stream many times. */
 ocp_status ocp_batch_tune(ocp_batch* batch, double dt, int reps, ocp_launch_shape* best, void* cuda_stream);
 ocp_status ocp_batch_set_shape(ocp_batch* batch, const ocp_launch_shape* shape);
@@ -269,10 +277,16 @@ ocp_status ocp_batch_get_status(ocp_batch* batch, void* cuda_stream);
  * CTA per tile and the largest tiles (128 cells for the cell and face stages,
  * 256 for assembly) that still give every SM two CTAs, halving down to 32
  * cells for small grids; grids of fewer than 64 cells per SM start with
- * ordered = 3. */
+ * ordered = 3, and grids that fit one cluster (ocp_grid_cluster_tiles) with
+ * ordered = 4. */
 ocp_status ocp_grid_set_shape(ocp_grid* grid, const ocp_launch_shape* shape);
 /* The launch shape ocp_linearize currently uses on the grid. */
 ocp_status ocp_grid_get_shape(const ocp_grid* grid, ocp_launch_shape* shape);
+/* *tiles = the largest grid, in 32-cell tiles, that ordered = 4 accepts on
+ * the grid's device: the largest thread-block cluster of the one-cluster
+ * kernel the device can run, at most 16 (0 if none).  No counterpart in
+ * the paper: a property of the launch, not of the method. */
+ocp_status ocp_grid_cluster_tiles(const ocp_grid* grid, int* tiles);
 
 /* ---------------------------------------------------------------- Newton step
  * The rest of the FIM nonlinear iteration of Sec. 3.2.5 -- the linear solve

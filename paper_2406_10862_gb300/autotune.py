@@ -24,8 +24,8 @@ def _key(batch):
     g0 = batch.grids[0]
     ncell = sum(g.N for g in batch.grids)
     name = torch.cuda.get_device_name(g0.device).replace(" ", "_")
-    # "ordered": the tuner also times the ordered (persistent) launches
-    return "%s|nb%d|cells2^%d|models2^%d|ordered" % (name, g0.nb, int(round(math.log2(max(ncell, 1)))),
+    # "ordered|cluster": the tuner also times the ordered (persistent) and one-cluster launches
+    return "%s|nb%d|cells2^%d|models2^%d|ordered|cluster" % (name, g0.nb, int(round(math.log2(max(ncell, 1)))),
                                                    int(round(math.log2(len(batch.grids)))))
 
 

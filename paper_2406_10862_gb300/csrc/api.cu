@@ -237,6 +237,7 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   P.vol_rb = d->dx * d->dy * d->dz / ocp::kRbFt3;
 
   g->sms = 0;
+  g->max_cluster = 0;
   g->dx = d->dx;
   g->dy = d->dy;
   g->kz_over_kx = d->kz_over_kx;
@@ -280,6 +281,10 @@ ocp_status ocp_grid_create(const ocp_grid_desc* d, int device, ocp_grid** out) {
   // allocates anyway) so that that entry point never triggers a lazy load
   if (e == cudaSuccess) e = ocp::static_scratch_address(&g->d_static_scratch);
   if (e == cudaSuccess) e = ocp::preload_linearize(nb);
+  if (e == cudaSuccess) {           // small grids may run as one cluster launch
+    g->max_cluster = ocp::cluster_max_tiles(nb);
+    g->cfg = ocp::default_cfg(N, g->sms, g->max_cluster);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(d_lnk);
   if (e != cudaSuccess) {

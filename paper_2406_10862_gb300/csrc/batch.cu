@@ -92,11 +92,16 @@ cudaError_t upload(ocp_batch* b, double dt, cudaStream_t s) {
   return e;
 }
 
+// The largest one-cluster launch a batch may take: only a batch of one
+// grid, and only as large as its device runs.
+int cluster_tiles(const ocp_batch* b) { return b->grids.size() == 1 ? b->grids[0]->max_cluster : 0; }
+
 cudaError_t run_cfg(ocp_batch* b, const ocp::LaunchCfg& cfg, cudaStream_t s) {
   ocp::TileList L[ocp::kNumTileSizes];
   lists_of(b, L);
   ocp::ModelArgs unused{};
   if (cfg.ordered == 0 || cfg.ordered == 3) return ocp::launch_tiles(b->nb, L, unused, cfg, b->sms, s);
+  if (cfg.ordered == 4) return ocp::launch_cluster(b->nb, b->d_models, unused, b->grids[0]->prm.N, cluster_tiles(b), s);
   const int ti = ocp::tile_index(cfg.tpb[1]);
   if (ti < 0) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(unsigned) * (1 + 2 * b->nsync_tiles), s);
@@ -123,7 +128,16 @@ ocp_status check_shape(const ocp_launch_shape* sh) {
     if (sh->ctas_per_sm[s] < 0 || sh->ctas_per_sm[s] > 64)
       return ocp::report(OCP_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
   }
-  if (sh->ordered < 0 || sh->ordered > 3) return ocp::report(OCP_ERR_INVALID_ARG, "ordered must be 0, 1, 2 or 3");
+  if (sh->ordered < 0 || sh->ordered > 4) return ocp::report(OCP_ERR_INVALID_ARG, "ordered must be 0, 1, 2, 3 or 4");
+  return OCP_OK;
+}
+
+// ordered = 4 needs a model of at most `max_tiles` 32-cell tiles.
+ocp_status check_cluster(const ocp_launch_shape* sh, long long N, int max_tiles) {
+  if (sh->ordered == 4 && (N + 31) / 32 > max_tiles)
+    return ocp::report(OCP_ERR_INVALID_ARG,
+                       "ordered = 4 needs one grid of at most %d 32-cell tiles on this device (has %lld)", max_tiles,
+                       (N + 31) / 32);
   return OCP_OK;
 }
 
@@ -147,7 +161,7 @@ ocp_status ocp_batch_create(ocp_grid* const* grids, int n, ocp_batch** out) {
   b->sms = grids[0]->sms;
   b->grids.assign(grids, grids + n);
   for (int m = 0; m < n; ++m) b->ncell += grids[m]->prm.N;
-  b->cfg = ocp::default_cfg(b->ncell, b->sms);    // until tuned or set
+  b->cfg = ocp::default_cfg(b->ncell, b->sms, n == 1 ? grids[0]->max_cluster : 0);    // until tuned or set
   // largest models first
   std::vector<int> order(n);
   for (int m = 0; m < n; ++m) order[m] = m;
@@ -260,6 +274,7 @@ ocp_status ocp_batch_graph_launch(ocp_batch* b, double dt, void* stream) {
 ocp_status ocp_batch_set_shape(ocp_batch* b, const ocp_launch_shape* sh) {
   if (!b) return ocp::report(OCP_ERR_INVALID_ARG, "batch is NULL");
   ocp_status st = check_shape(sh);
+  if (st == OCP_OK) st = check_cluster(sh, b->grids.size() == 1 ? b->grids[0]->prm.N : b->ncell, cluster_tiles(b));
   if (st != OCP_OK) return st;
   for (int s = 0; s < 3; ++s) {
     b->cfg.tpb[s] = sh->cells_per_tile[s];
@@ -301,6 +316,7 @@ ocp_status ocp_batch_tune(ocp_batch* b, double dt, int reps, ocp_launch_shape* b
   lists_of(b, L);
   ocp::ModelArgs unused{};
   ocp::LaunchCfg cur = b->cfg;
+  cur.ordered = 0;                      // the stages are tuned as three plain launches
   for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
     float best_ms = 1e30f;
     ocp::LaunchCfg pick = cur;
@@ -362,9 +378,10 @@ ocp_status ocp_batch_tune(ocp_batch* b, double dt, int reps, ocp_launch_shape* b
     time_pass(cur, best_ms);
     const int octas[4] = {0, 1, 2, 4};
     ocp::LaunchCfg base = cur;
-    {                                   // the split face and assembly stages
+    for (int mode = 3; mode <= 4 && e == cudaSuccess; ++mode) {   // the split face and assembly stages,
+      if (mode == 4 && (b->ncell + 31) / 32 > cluster_tiles(b)) break;   // as three launches or one cluster
       ocp::LaunchCfg c = base;
-      c.ordered = 3;
+      c.ordered = mode;
       c.ctas_per_sm[1] = c.ctas_per_sm[2] = 0;
       float ms = 1e30f;
       time_pass(c, ms);
@@ -414,6 +431,7 @@ ocp_status ocp_batch_get_status(ocp_batch* b, void* stream) {
 ocp_status ocp_grid_set_shape(ocp_grid* g, const ocp_launch_shape* sh) {
   if (!g) return ocp::report(OCP_ERR_INVALID_ARG, "grid is NULL");
   ocp_status st = check_shape(sh);
+  if (st == OCP_OK) st = check_cluster(sh, g->prm.N, g->max_cluster);
   if (st != OCP_OK) return st;
   for (int s = 0; s < 3; ++s) {
     g->cfg.tpb[s] = sh->cells_per_tile[s];
@@ -430,6 +448,12 @@ ocp_status ocp_grid_get_shape(const ocp_grid* g, ocp_launch_shape* sh) {
     sh->ctas_per_sm[s] = g->cfg.ctas_per_sm[s];
   }
   sh->ordered = g->cfg.ordered;
+  return OCP_OK;
+}
+
+ocp_status ocp_grid_cluster_tiles(const ocp_grid* g, int* tiles) {
+  if (!g || !tiles) return ocp::report(OCP_ERR_INVALID_ARG, "grid and tiles are required");
+  *tiles = g->max_cluster;
   return OCP_OK;
 }
 

@@ -52,6 +52,11 @@ cudaError_t launch_tiles(int nb, const TileList* lists, const ModelArgs& single,
 // The ordered (persistent) launch; O.nitems holds the number of tiles.
 cudaError_t launch_ordered(int nb, const TileList* lists, OrderedList O, const ModelArgs& single,
                            const LaunchCfg& cfg, int sms, cudaStream_t s);
+// The one-cluster launch of a small grid (at most max_tiles 32-cell tiles):
+// the first model of `models`, or `single` when models is null.
+cudaError_t launch_cluster(int nb, const ModelArgs* models, const ModelArgs& single, long long N, int max_tiles,
+                           cudaStream_t s);
+int cluster_max_tiles(int nb);
 ModelArgs model_args(const ocp_grid* g, double* scratch, const double* u_new, const int8_t* f_new,
                      const double* u_old, const int8_t* f_old, double dt, double* res, double* val,
                      double* face_flux);

@@ -98,9 +98,12 @@ __device__ __forceinline__ void cell_body(const ModelArgs& M, const Table& T, lo
   if (!M.no_acc) {
     double mo[3];
     cell_masses<NB, false>(P, T, po, swo, xo, fo & 1, phs, mo);
+    // explicitly rounded differences here and below: the terms may come
+    // from other warps (the one-cluster launch), so that no product is ever
+    // fused into these subtractions and every launch shape gives the same bits
 #pragma unroll
     for (int e = 0; e < NB; ++e) {
-      r[e] = a.m[e] - mo[e];
+      r[e] = __dsub_rn(a.m[e], mo[e]);
       dg[e][0] = a.m_p[e];
       dg[e][1] = a.m_sw[e];
       dg[e][2] = a.m_x[e];
@@ -115,8 +118,8 @@ __device__ __forceinline__ void cell_body(const ModelArgs& M, const Table& T, lo
     if (M.p_bh) w.p_bh = M.p_bh[w.well];
     well_source<NB>(w, q, a, src, ds);
     for (int e = 0; e < NB; ++e) {
-      r[e] -= src[e];
-      for (int v = 0; v < NB; ++v) dg[e][v] -= ds[e][v];
+      r[e] = __dsub_rn(r[e], src[e]);
+      for (int v = 0; v < NB; ++v) dg[e][v] = __dsub_rn(dg[e][v], ds[e][v]);
     }
   }
   store_q<NB>(scr, N, c, q);
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(TPB) assemble_kernel(TileList L, ModelArgs sin
 
 // Face d of cell c: the blocks and the + neighbour's share as in face_part;
 // this row's own terms (F, dF/du_c) go to own[0..12)[lane] for the combine.
-template <int NB>
+template <int NB, bool COH>
 __device__ __forceinline__ void face_dir(const ModelArgs& M, long long c, int d, double (*own)[32], int lane) {
   constexpr int B2 = NB * NB;
   const Params& P = M.P;
@@ -351,8 +354,8 @@ __device__ __forceinline__ void face_dir(const ModelArgs& M, long long c, int d,
   const long long stride = d == 0 ? 1 : (d == 1 ? (long long)P.nx : P.nxy);
   const long long n = c + stride;
   CellQ a, b;
-  load_q<NB>(scr, N, c, a);
-  load_q<NB>(scr, N, n, b);
+  load_q<NB, COH>(scr, N, c, a);
+  load_q<NB, COH>(scr, N, n, b);
   FaceOut<NB> o;
   const double T = M.trans[d * N + c];
   if (d == 2) face_terms<NB, true>(T, -P.grav_dz, a, b, o);
@@ -377,41 +380,84 @@ __device__ __forceinline__ void face_dir(const ModelArgs& M, long long c, int d,
   }
 }
 
+// One 32-cell tile of the split face stage (96 threads): warp d computes
+// direction d of every cell of the tile, then warp e < NB adds equation e's
+// own terms and faces x, y, z.  Ends with the own[] buffer free again.
+template <int NB, bool COH>
+__device__ __forceinline__ void face_split_tile(const ModelArgs& M, long long c0, double (*own)[12][32]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long N = M.P.N;
+  const long long c = c0 + lane;
+  if (c < N) face_dir<NB, COH>(M, c, w, own[w], lane);
+  __syncthreads();
+  if (c < N && w < NB) {               // warp e: equation e of this row, own terms + faces x, y, z
+    int i, j, k;
+    cell_ijk(M.P, c, i, j, k);
+    const bool hp[3] = {i + 1 < M.P.nx, j + 1 < M.P.ny, k + 1 < M.P.nz};
+    double* scr = M.scr;
+    const int e = w;
+    double r = lds<COH>(scr + (kSelf + e) * N + c);
+    double dg[NB];
+#pragma unroll
+    for (int v = 0; v < NB; ++v) dg[v] = lds<COH>(scr + (kSelf + 3 + 3 * e + v) * N + c);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (!hp[d]) continue;
+      r += own[d][e][lane];
+#pragma unroll
+      for (int v = 0; v < NB; ++v) dg[v] += own[d][3 + 3 * e + v][lane];
+    }
+    scr[(kPart + e) * N + c] = r;
+#pragma unroll
+    for (int v = 0; v < NB; ++v) scr[(kPart + 3 + 3 * e + v) * N + c] = dg[v];
+  }
+  __syncthreads();                     // own[] is free for the next tile
+}
+
+// Equation e of row c in the split assembly: its own terms and + faces
+// minus the shares of the - neighbours, in the order -z, -y, -x.
+template <int NB, bool COH>
+__device__ __forceinline__ void assemble_finish(const ModelArgs& M, long long c, int e, double r, double (&dg)[NB]) {
+  const long long N = M.P.N;
+  const double* scr = M.scr;
+  int i, j, k;
+  cell_ijk(M.P, c, i, j, k);
+  const bool hm[3] = {i > 0, j > 0, k > 0};
+#pragma unroll
+  for (int d = 2; d >= 0; --d) {
+    if (!hm[d]) continue;
+    const int base = kInc + 12 * d;
+    r -= lds<COH>(scr + (base + e) * N + c);
+#pragma unroll
+    for (int v = 0; v < NB; ++v) dg[v] -= lds<COH>(scr + (base + 3 + 3 * e + v) * N + c);
+  }
+  double* out = M.val + (row_start_ijk(M.P, c, i, j, k) + (int)hm[0] + (int)hm[1] + (int)hm[2]) * NB * NB;
+  __stcs(M.res + c * NB + e, r);
+#pragma unroll
+  for (int v = 0; v < NB; ++v) __stcs(out + e * NB + v, dg[v]);
+  if (!finite(r)) atomicOr(M.status, kStatNonFinite);
+}
+
+template <int NB, bool COH>
+__device__ __forceinline__ void assemble_split_row(const ModelArgs& M, long long c, int e) {
+  const long long N = M.P.N;
+  const double* scr = M.scr;
+  const double r = lds<COH>(scr + (kPart + e) * N + c);
+  double dg[NB];
+#pragma unroll
+  for (int v = 0; v < NB; ++v) dg[v] = lds<COH>(scr + (kPart + 3 + 3 * e + v) * N + c);
+  assemble_finish<NB, COH>(M, c, e, r, dg);
+}
+
 template <int NB>
 __global__ void __launch_bounds__(96) face_split_kernel(TileList L, ModelArgs single) {
   pdl_wait();
   __shared__ double own[3][12][32];      // [direction][F, dF/du_c][lane]
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int t = blockIdx.x; t < L.ntiles; t += gridDim.x) {
     int m;
     long long c0;
     const ModelArgs& M = tile_of<32>(L, single, t, m, c0);
-    const long long N = M.P.N;
-    const long long c = c0 + lane;
-    if (c < N) face_dir<NB>(M, c, w, own[w], lane);
-    __syncthreads();
-    if (c < N && w < NB) {               // warp e: equation e of this row, own terms + faces x, y, z
-      int i, j, k;
-      cell_ijk(M.P, c, i, j, k);
-      const bool hp[3] = {i + 1 < M.P.nx, j + 1 < M.P.ny, k + 1 < M.P.nz};
-      double* scr = M.scr;
-      const int e = w;
-      double r = scr[(kSelf + e) * N + c];
-      double dg[NB];
-#pragma unroll
-      for (int v = 0; v < NB; ++v) dg[v] = scr[(kSelf + 3 + 3 * e + v) * N + c];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (!hp[d]) continue;
-        r += own[d][e][lane];
-#pragma unroll
-        for (int v = 0; v < NB; ++v) dg[v] += own[d][3 + 3 * e + v][lane];
-      }
-      scr[(kPart + e) * N + c] = r;
-#pragma unroll
-      for (int v = 0; v < NB; ++v) scr[(kPart + 3 + 3 * e + v) * N + c] = dg[v];
-    }
-    __syncthreads();                     // own[] is reused by the next tile
+    face_split_tile<NB, false>(M, c0, own);
   }
 }
 
@@ -424,31 +470,549 @@ __global__ void __launch_bounds__(96) assemble_split_kernel(TileList L, ModelArg
     int m;
     long long c0;
     const ModelArgs& M = tile_of<32>(L, single, t, m, c0);
-    const long long N = M.P.N;
     const long long c = c0 + lane;
-    if (c >= N) continue;
-    const double* scr = M.scr;
-    int i, j, k;
-    cell_ijk(M.P, c, i, j, k);
-    const bool hm[3] = {i > 0, j > 0, k > 0};
-    double r = scr[(kPart + e) * N + c];
-    double dg[NB];
-#pragma unroll
-    for (int v = 0; v < NB; ++v) dg[v] = scr[(kPart + 3 + 3 * e + v) * N + c];
-#pragma unroll
-    for (int d = 2; d >= 0; --d) {
-      if (!hm[d]) continue;
-      const int base = kInc + 12 * d;
-      r -= scr[(base + e) * N + c];
-#pragma unroll
-      for (int v = 0; v < NB; ++v) dg[v] -= scr[(base + 3 + 3 * e + v) * N + c];
-    }
-    double* out = M.val + (row_start_ijk(M.P, c, i, j, k) + (int)hm[0] + (int)hm[1] + (int)hm[2]) * NB * NB;
-    __stcs(M.res + c * NB + e, r);
-#pragma unroll
-    for (int v = 0; v < NB; ++v) __stcs(out + e * NB + v, dg[v]);
-    if (!finite(r)) atomicOr(M.status, kStatNonFinite);
+    if (c < M.P.N) assemble_split_row<NB, false>(M, c, e);
   }
+}
+
+// -------------------------------------------------------- one-cluster launch
+// A grid of at most kMaxClusterTiles 32-cell tiles linearised by one
+// thread-block cluster, CTA t (cluster rank t) owning tile t, in three
+// stages separated by cluster barriers instead of launch boundaries.  The
+// stages exchange data through distributed shared memory rather than
+// scratch: each CTA keeps its cells' quantities in its own shared memory,
+// where the face stage of the CTA holding a - neighbour reads them, and that
+// face stage writes the neighbour's share straight into the shared memory of
+// the CTA owning the neighbour.  barrier.cluster.arrive.release orders those
+// accesses before barrier.cluster.wait.acquire returns in every CTA; a CTA
+// arrives as soon as its writes for the others are done and waits only
+// before it reads theirs, doing its own CTA's work in between.  Every thread
+// reaches every barrier, and no CTA touches another's shared memory after
+// the last one.
+//
+// Such grids are latency bound: each FP64 warp instruction holds an SM
+// sub-partition's FP64 unit 64 cycles, so a stage takes about the FP64
+// instruction count of its busiest sub-partition.  Both stages are
+// therefore spread over more warps than the tile kernels use:
+//   cell stage: warp 0 the PVT properties at the new state, warp 1 the
+//   relative permeabilities, warp 3 the amounts at the old state; then
+//   warp 0 the water and oil amounts and accumulation terms, warp 3 the gas
+//   ones, warp 2 the densities, mobilities and well terms, warp 1 the
+//   capillary pressures;
+//   face stage: one warp per direction and phase, placed so that the four
+//   sub-partitions get about equal FP64 work, the gas component's
+//   dissolved-gas term added by the gas warp once the oil warp's phase flux
+//   is in shared memory; then one warp per equation adds the faces to the
+//   cell's own terms and, after the second barrier, subtracts the shares of
+//   the - neighbours.
+// Every quantity is computed by the same expressions as in the tile kernels
+// (the differences that take terms computed by other warps are explicitly
+// rounded there too), so the results are bit-identical to theirs.
+constexpr int kClusterThreads = 288;   // 9 warps: 3 directions x 3 phases in the face stage
+
+struct ClusterCellBuf {                // cell stage, per lane
+  Pvt f[32];                           // warp 0 -> warps 1, 2, 3
+  KrSide kg[32];                       // warp 2 -> warp 1
+  Kr k[32];                            // warp 1 -> warp 2
+  double mo[3][32];                    // warp 3 -> warps 0, 3
+  double src[3][32], ds[3][3][32];     // warps 1, 2 -> warps 0, 3 (perforated cells)
+  double qg[3][32];                    // warp 1 -> warp 2: producers' free-gas rate
+};
+struct ClusterFaceBuf {                // face stage, per lane
+  double own[3][12][32];               // [direction][F, dF/du_c][lane]
+  double oil[3][7][32];                // [direction][F, di, dj of the oil phase][lane]
+  int up_o[3][32];
+};
+struct ClusterShared {                 // read and written by the other CTAs of the cluster
+  double q[kQ][32];                    // CellQ fields of the tile's cells
+  double share[3][12][32];             // [direction][F, dF/du_-][lane]: the - neighbour's share
+};
+// The Jacobian rows of the tile's cells are assembled in shared memory (the
+// - neighbour blocks written there by the CTAs holding those neighbours) and
+// stored with coalesced stores at the end: at most 7 blocks per row.  The
+// dynamic shared memory is sized above half an SM's so that the CTAs of the
+// cluster run on different SMs (their FP64 units set the time).
+constexpr int kClusterStageBlocks = 32 * 7;
+constexpr int kClusterDynSmem = 120 * 1024;
+static_assert(kClusterStageBlocks * 9 * (int)sizeof(double) <= kClusterDynSmem, "staged rows exceed the buffer");
+// Block index of the first block of row c, for 0 <= c <= N (N: the total).
+__device__ __forceinline__ long long row_start_any(const Params& P, long long c) {
+  if (c >= P.N) return 7 * P.N - 2 * ((long long)P.ny * P.nz + (long long)P.nx * P.nz + P.nxy);
+  int i, j, k;
+  cell_ijk(P, c, i, j, k);
+  return row_start_ijk(P, c, i, j, k);
+}
+
+// Face-stage task of warp w: direction kTaskD, phase kTaskPh (0 water, 1
+// oil, 2 gas; -1 none).  Warp w runs on sub-partition w % 4; with three
+// phases each sub-partition gets about 50 FP64 instructions per cell (a gas
+// task, which also adds the dissolved gas, counts for about two others).
+// Two bits per warp, warp w at bits 2w: three phases d = 0 0 1 2 1 1 2 2 0,
+// ph = 0 2 2 2 0 1 1 0 1; two phases d = 0 0 1 1 2 2, ph = 0 1 0 1 1 0, and
+// 3 (none) for warps 6..8.
+__device__ __forceinline__ void face_task(int nb, int w, int& d, int& ph) {
+  const unsigned dk = nb == 3 ? 42384u : 2640u, pk = nb == 3 ? 70824u : 258372u;
+  d = (int)((dk >> (2 * w)) & 3u);
+  ph = (int)((pk >> (2 * w)) & 3u);
+  if (ph == 3) ph = -1;
+}
+
+// The cluster barrier in its two halves.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Distributed shared memory: the address of `p` (a variable of this CTA's
+// shared memory) in the window of cluster rank `rank`, and 8-byte accesses
+// through such addresses.
+__device__ __forceinline__ unsigned dsmem_addr(const void* p, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ double dsmem_ld(unsigned a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void dsmem_st(unsigned a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+
+// CellQ fields [lo, hi) that the block size uses, into the tile's q[][lane].
+template <int NB>
+__device__ __forceinline__ void put_q(double (*qs)[32], int lane, const CellQ& q, int lo, int hi) {
+  const double* f = reinterpret_cast<const double*>(&q);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i)
+    if (i >= lo && i < hi && q_used<NB>(i)) qs[i][lane] = f[i];
+}
+// The CellQ fields of one phase (0 water, 1 oil, 2 gas with the dissolved-gas
+// ratio; the others left zero) of lane `lane` of the tile whose q[][] is at
+// cluster address `a` (dsmem_addr of q[0][0]).
+__host__ __device__ constexpr bool q_of_phase(int i, int ph) {
+  // water pw dpw_sw rw rw_p lw lw_p lw_sw; oil p ro ro_p ro_x lo lo_p lo_sw lo_x;
+  // gas pg dpg_x rg rg_p lg lg_p lg_x rs rs_p rs_x
+  const bool w = i == 1 || i == 3 || i == 5 || i == 6 || i == 12 || i == 13 || i == 14;
+  const bool o = i == 0 || i == 7 || i == 8 || i == 9 || i == 15 || i == 16 || i == 17 || i == 18;
+  const bool g = i == 2 || i == 4 || i == 10 || i == 11 || i == 19 || i == 20 || i == 21 || i >= 22;
+  return ph == 0 ? w : (ph == 1 ? o : g);
+}
+template <int NB, int PH>
+__device__ __forceinline__ void get_q_phase(unsigned a, int lane, CellQ& q) {
+  double* f = reinterpret_cast<double*>(&q);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) f[i] = (q_of_phase(i, PH) && q_used<NB>(i)) ? dsmem_ld(a + 8u * (32u * i + lane)) : 0.0;
+}
+// The quantities of phase PH of this cell (a, this CTA) and of its +
+// neighbour (b, lane ln of CTA rank), and the phase's flux across the face.
+template <int NB, int PH>
+__device__ __forceinline__ void phase_face(unsigned qa, int lane, unsigned qb, int ln, bool grav, double T,
+                                           double hz, CellQ& a, CellQ& b, double& F, double (&di)[3],
+                                           double (&dj)[3], bool& up) {
+  get_q_phase<NB, PH>(qa, lane, a);
+  get_q_phase<NB, PH>(qb, ln, b);
+  if (PH == 0) {
+    if (grav) water_flux<NB, true>(T, hz, a, b, F, di, dj, up);
+    else water_flux<NB, false>(T, hz, a, b, F, di, dj, up);
+  } else if (PH == 1) {
+    if (grav) oil_flux<NB, true>(T, hz, a, b, F, di, dj, up);
+    else oil_flux<NB, false>(T, hz, a, b, F, di, dj, up);
+  } else {
+    if (grav) gas_flux<NB, true>(T, hz, a, b, F, di, dj, up);
+    else gas_flux<NB, false>(T, hz, a, b, F, di, dj, up);
+  }
+}
+
+// A cell's inputs, loaded by each cell-stage warp before it waits for the
+// PVT table (one round of memory latency).
+struct CellIn {
+  double pn, swn, xn, po, swo, xo, phs;
+  int fn, fo, ip;
+};
+template <int NB>
+__device__ __forceinline__ void load_cell_in(const ModelArgs& M, long long c, CellIn& in) {
+  const long long N = M.P.N;
+  in.pn = M.u_new[c];
+  in.swn = M.u_new[N + c];
+  in.xn = (NB == 3) ? M.u_new[2 * N + c] : 0.0;
+  in.po = M.u_old[c];
+  in.swo = M.u_old[N + c];
+  in.xo = (NB == 3) ? M.u_old[2 * N + c] : 0.0;
+  in.fn = (NB == 3) ? M.f_new[c] : 0;
+  in.fo = (NB == 3) ? M.f_old[c] : 0;
+  in.phs = M.phi[c] * M.scale;
+  in.ip = M.perf_of_cell[c];
+}
+
+// Barrier of warps 1 and 2 only (named barrier `id`, 64 threads).
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// The cell stage of tile c0 (warps 0..3, one cell per lane): the cells'
+// quantities go to qs, their own residual and diagonal block to self.
+// Phase A: warp 0 the PVT properties at the new state, warps 1 and 2 the
+// water and gas sides of the relative permeabilities (warp 1 then combines
+// them), warp 3 the amounts at the old state.  Phase B: warp 0 the water and
+// oil amounts and their accumulation terms, warp 3 the gas ones, warp 1 the
+// capillary pressures and the water and gas densities and mobilities, warp 2
+// the oil ones and (tiles with perforated cells) the well terms.  Phase C
+// (such tiles): warps 0 and 3 subtract the well terms.
+template <int NB>
+__device__ __forceinline__ void cluster_cell_stage(const ModelArgs& M, const Table& T, long long c0,
+                                                   const CellIn& in, ClusterCellBuf& B, double (*qs)[32],
+                                                   double (*self)[32]) {
+  const Params& P = M.P;
+  const long long N = P.N;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long c = c0 + lane;
+  const bool live = c < N;
+  const int ip = (live && w < 4) ? in.ip : -1;
+  const double pn = in.pn, swn = in.swn, phs = in.phs;
+  const int flag = in.fn & 1;
+  const bool tile_well = __any_sync(0xffffffffu, ip >= 0);   // the same in warps 0..3
+  Pvt f;
+  Kr k;
+  if (w == 0) {                         // PVT at the new state
+    if (live) {
+      int bad = 0;
+      if (!(finite(pn) && finite(swn) && finite(in.xn) && finite(in.po) && finite(in.swo) && finite(in.xo)))
+        bad |= kStatNonFinite;
+      if ((unsigned)in.fn > 1u || (unsigned)in.fo > 1u) bad |= kStatBadFlag;
+      if (bad) atomicOr(M.status, bad);
+      pvt<NB, true>(P, T, pn, in.xn, flag, f);
+      B.f[lane] = f;
+    }
+  } else if (w == 1) {                  // relative permeabilities: water side, then both
+    KrSide kw;
+    if (live) rel_perm_w(P, swn, kw);
+    if (NB == 3) pair_sync(1);
+    if (live) {
+      KrSide kg{};
+      if (NB == 3) kg = B.kg[lane];
+      rel_perm_combine<NB>(P, kw, kg, flag, k);
+      B.k[lane] = k;
+    }
+  } else if (w == 2) {                  // relative permeabilities: gas side
+    if (NB == 3) {
+      if (live) {
+        KrSide kg;
+        rel_perm_g(P, flag == 0 ? in.xn : 0.0, kg);
+        B.kg[lane] = kg;
+      }
+      pair_sync(1);
+    }
+  } else if (w == 3 && live && !M.no_acc) {   // the amounts at the old state
+    double mo[3];
+    cell_masses<NB, false>(P, T, in.po, in.swo, in.xo, in.fo & 1, phs, mo);
+#pragma unroll
+    for (int e = 0; e < NB; ++e) B.mo[e][lane] = mo[e];
+  }
+  __syncthreads();
+  // rows e0 <= e < e1 of the own terms: warp 0 water and oil, warp 3 gas
+  const int e0 = w == 0 ? 0 : 2, e1 = w == 0 ? 2 : NB;
+  const bool rows = live && (w == 0 || (NB == 3 && w == 3));
+  double r[3] = {0.0, 0.0, 0.0}, dg[3][3] = {};
+  if (rows) {
+    if (w == 3) f = B.f[lane];
+    double m[3], m_p[3], m_sw[3], m_x[3];
+    if (w == 0) masses<NB, true, 0>(P, f, pn, swn, phs, m, m_p, m_sw, m_x);
+    else masses<NB, true, 1>(P, f, pn, swn, phs, m, m_p, m_sw, m_x);
+#pragma unroll
+    for (int e = 0; e < NB; ++e) {
+      if (e < e0 || e >= e1) continue;
+      if (!M.no_acc) {
+        r[e] = __dsub_rn(m[e], B.mo[e][lane]);
+        dg[e][0] = m_p[e];
+        dg[e][1] = m_sw[e];
+        dg[e][2] = m_x[e];
+      } else {
+        r[e] = dg[e][0] = dg[e][1] = dg[e][2] = 0.0;
+      }
+    }
+  } else if (w == 1) {                  // capillary pressures, water and gas densities and mobilities
+    if (live) {
+      f = B.f[lane];
+      CellQ q{};
+      cap_pressure<NB>(P, pn, k, q);
+      dens_mob<NB, true, false>(P, f, k, q);
+      put_q<NB>(qs, lane, q, 0, 7);      // p pw pg dpw_sw dpg_x rw rw_p
+      put_q<NB>(qs, lane, q, 10, 15);    // rg rg_p lw lw_p lw_sw
+      put_q<NB>(qs, lane, q, 19, kQ);    // lg lg_p lg_x rs rs_p rs_x
+      if (ip >= 0) {                    // producers: the water row and the free gas
+        Perf wl = M.perf[ip];
+        if (M.p_bh) wl.p_bh = M.p_bh[wl.well];
+        if (wl.kind == 0) {
+          double src = 0.0, d[3] = {0.0, 0.0, 0.0}, qg[3] = {0.0, 0.0, 0.0};
+          if (positive(q.p - wl.p_bh)) {
+            const double g = wl.p_bh - q.p;
+            well_prod_water(wl, q, g, src, d);
+            if (NB == 3) well_prod_gas_free(wl, q, g, qg);
+          }
+          B.src[0][lane] = src;
+#pragma unroll
+          for (int v = 0; v < NB; ++v) B.ds[0][v][lane] = d[v];
+#pragma unroll
+          for (int v = 0; v < 3; ++v) B.qg[v][lane] = qg[v];
+        }
+      }
+    }
+    if (tile_well) pair_sync(2);
+  } else if (w == 2) {                  // oil density and mobility, well terms
+    CellQ q{};
+    if (live) {
+      f = B.f[lane];
+      k = B.k[lane];
+      dens_mob<NB, false, true>(P, f, k, q);
+      put_q<NB>(qs, lane, q, 7, 10);     // ro, ro_p, ro_x
+      put_q<NB>(qs, lane, q, 15, 19);    // lo, lo_p, lo_sw, lo_x
+    }
+    if (tile_well) {
+      Perf wl{};
+      double src[3] = {0.0, 0.0, 0.0}, ds[3][3] = {};
+      bool prod = false;
+      if (ip >= 0) {
+        wl = M.perf[ip];
+        if (M.p_bh) wl.p_bh = M.p_bh[wl.well];
+        q.p = pn;
+        prod = wl.kind == 0 && positive(q.p - wl.p_bh);
+        if (prod) well_prod_oil(wl, q, wl.p_bh - q.p, src[1], ds[1]);
+      }
+      pair_sync(2);
+      if (ip >= 0) {
+        if (wl.kind == 0) {             // producers: the oil row, then the gas component
+          if (NB == 3 && prod) {
+            q.rs = qs[22][lane];
+            q.rs_p = qs[23][lane];
+            q.rs_x = qs[24][lane];
+            const double qg[3] = {B.qg[0][lane], B.qg[1][lane], B.qg[2][lane]};
+            well_prod_gas(q, src[1], ds[1], qg, src[2], ds[2]);
+          }
+#pragma unroll
+          for (int e = 1; e < NB; ++e) {
+            B.src[e][lane] = src[e];
+#pragma unroll
+            for (int v = 0; v < NB; ++v) B.ds[e][v][lane] = ds[e][v];
+          }
+        } else {                        // injectors: the injected phase's row
+          CellQ qa;
+          double* fq = reinterpret_cast<double*>(&qa);
+#pragma unroll
+          for (int i = 0; i < kQ; ++i) fq[i] = q_used<NB>(i) ? qs[i][lane] : 0.0;
+          qa.p = pn;
+          CellAux a{};
+          total_mob<NB>(P, f, k, true, a);
+          well_source<NB>(wl, qa, a, src, ds);
+#pragma unroll
+          for (int e = 0; e < NB; ++e) {
+            B.src[e][lane] = src[e];
+#pragma unroll
+            for (int v = 0; v < NB; ++v) B.ds[e][v][lane] = ds[e][v];
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (rows) {                           // minus the well terms; own terms to shared memory
+    if (ip >= 0) {
+#pragma unroll
+      for (int e = 0; e < NB; ++e) {
+        if (e < e0 || e >= e1) continue;
+        r[e] = __dsub_rn(r[e], B.src[e][lane]);
+#pragma unroll
+        for (int v = 0; v < NB; ++v) dg[e][v] = __dsub_rn(dg[e][v], B.ds[e][v][lane]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < NB; ++e) {
+      if (e < e0 || e >= e1) continue;
+      self[e][lane] = r[e];
+#pragma unroll
+      for (int v = 0; v < NB; ++v) self[3 + 3 * e + v][lane] = dg[e][v];
+    }
+  }
+}
+
+// Row e of face d's outputs (as face_dir writes them for every row): this
+// row's block of the neighbour into the tile's staged rows at blk, the
+// neighbour row's block of this cell at cluster address nblk and the
+// neighbour's share at cluster address sh (share[d][0][lane of the
+// neighbour]), both in the CTA holding the neighbour.
+template <int NB>
+__device__ __forceinline__ void face_row(const ModelArgs& M, long long c, int d, int e, double* blk, unsigned nblk,
+                                         double F, const double (&di)[3], const double (&dj)[3], double (*own)[32],
+                                         int lane, unsigned sh) {
+  const long long N = M.P.N;
+  own[e][lane] = F;
+  dsmem_st(sh + 256u * e, F);
+#pragma unroll
+  for (int v = 0; v < NB; ++v) {
+    own[3 + 3 * e + v][lane] = di[v];
+    blk[e * NB + v] = dj[v];
+    dsmem_st(nblk + 8u * (e * NB + v), neg(di[v]));
+    dsmem_st(sh + 256u * (3 + 3 * e + v), dj[v]);
+  }
+  if (M.face_flux) __stcs(M.face_flux + (d * NB + e) * N + c, F);
+}
+
+// The face stage of tile c0, entered after the CTA's arrival at the first
+// cluster barrier: warp w computes its task's phase of its direction for
+// every cell (Tf its face's transmissibility, loaded at the start of the
+// kernel); the CTA then arrives at the second barrier, and warp e < NB adds
+// its equation's faces to the own terms in self[] and returns them in r, dg.
+template <int NB>
+__device__ __forceinline__ void cluster_face_stage(const ModelArgs& M, long long c0, double Tf, ClusterFaceBuf& B,
+                                                   ClusterShared& S, double* stage, const double (*self)[32],
+                                                   double& r, double (&dg)[NB]) {
+  constexpr int B2 = NB * NB;
+  const Params& P = M.P;
+  const long long N = P.N;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long c = c0 + lane;
+  int d, ph;
+  face_task(NB, w, d, ph);
+  const bool active = c < N && ph >= 0;
+  int i = 0, j = 0, k = 0;
+  if (c < N) cell_ijk(P, c, i, j, k);
+  const bool hm[3] = {i > 0, j > 0, k > 0};
+  const bool hp[3] = {i + 1 < P.nx, j + 1 < P.ny, k + 1 < P.nz};
+  const bool has = active && hp[d];
+  const long long n = has ? c + (d == 0 ? 1 : (d == 1 ? (long long)P.nx : P.nxy)) : 0;
+  double* blk = nullptr;
+  unsigned nblk = 0;
+  CellQ a{}, b{};
+  double Fp = 0.0, di[3] = {0.0, 0.0, 0.0}, dj[3] = {0.0, 0.0, 0.0};
+  cluster_wait();                        // every CTA's cell quantities are in its shared memory
+  unsigned sh = 0;
+  if (active) {
+    if (!has) {
+      if (M.face_flux) __stcs(M.face_flux + (d * NB + ph) * N + c, 0.0);
+    } else {
+      const unsigned rank = (unsigned)(n >> 5), ln = (unsigned)(n & 31);
+      const unsigned qa = dsmem_addr(&S.q[0][0], blockIdx.x), qb = dsmem_addr(&S.q[0][0], rank);
+      sh = dsmem_addr(&S.share[d][0][ln], rank);
+      const double hz = d == 2 ? -P.grav_dz : 0.0;
+      bool up;
+      if (ph == 0) phase_face<NB, 0>(qa, lane, qb, (int)ln, d == 2, Tf, hz, a, b, Fp, di, dj, up);
+      else if (ph == 1) phase_face<NB, 1>(qa, lane, qb, (int)ln, d == 2, Tf, hz, a, b, Fp, di, dj, up);
+      else phase_face<NB, 2>(qa, lane, qb, (int)ln, d == 2, Tf, hz, a, b, Fp, di, dj, up);
+      const int slot = (int)hm[0] + (int)hm[1] + (int)hm[2] + 1 + (d > 0 && hp[0]) + (d > 1 && hp[1]);
+      blk = stage + (row_start_ijk(P, c, i, j, k) - row_start_any(P, c0) + slot) * B2;
+      const int slot_n = (d == 0) ? ((int)hm[2] + (int)hm[1]) : (d == 1 ? (int)hm[2] : 0);
+      const long long nb0 = row_start_any(P, (long long)rank * 32);
+      nblk = dsmem_addr(stage + (row_start_ijk(P, n, i + (d == 0), j + (d == 1), k + (d == 2)) - nb0 + slot_n) * B2,
+                        rank);
+      if (ph < 2) face_row<NB>(M, c, d, ph, blk, nblk, Fp, di, dj, B.own[d], lane, sh);
+      if (NB == 3 && ph == 1) {
+        B.oil[d][0][lane] = Fp;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          B.oil[d][1 + v][lane] = di[v];
+          B.oil[d][4 + v][lane] = dj[v];
+        }
+        B.up_o[d][lane] = up;
+      }
+    }
+  }
+  if (NB == 3) {
+    __syncthreads();
+    if (active && has && ph == 2) {     // the gas component: free gas plus gas dissolved in the oil
+      double di_o[3], dj_o[3], F, dig[3], djg[3];
+      const double Fo = B.oil[d][0][lane];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        di_o[v] = B.oil[d][1 + v][lane];
+        dj_o[v] = B.oil[d][4 + v][lane];
+      }
+      gas_component(a, b, B.up_o[d][lane] != 0, Fo, di_o, dj_o, Fp, di, dj, F, dig, djg);
+      face_row<NB>(M, c, d, 2, blk, nblk, F, dig, djg, B.own[d], lane, sh);
+    }
+  }
+  __syncthreads();
+  cluster_arrive();                      // this CTA's shares are in the other CTAs' shared memory
+  if (c < N && w < NB) {                // warp e: equation e, own terms + faces x, y, z
+    const int e = w;
+    r = self[e][lane];
+#pragma unroll
+    for (int v = 0; v < NB; ++v) dg[v] = self[3 + 3 * e + v][lane];
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      if (!hp[dd]) continue;
+      r += B.own[dd][e][lane];
+#pragma unroll
+      for (int v = 0; v < NB; ++v) dg[v] += B.own[dd][3 + 3 * e + v][lane];
+    }
+  }
+}
+
+// Equation e of row c: r, dg (own terms and + faces) minus the shares of the
+// - neighbours in share[][][lane], in the order -z, -y, -x (as
+// assemble_finish); the diagonal block goes to the staged rows.
+template <int NB>
+__device__ __forceinline__ void cluster_assemble(const ModelArgs& M, long long c0, long long c, int e, double r,
+                                                 double (&dg)[NB], const double (*share)[12][32], double* stage,
+                                                 int lane) {
+  int i, j, k;
+  cell_ijk(M.P, c, i, j, k);
+  const bool hm[3] = {i > 0, j > 0, k > 0};
+#pragma unroll
+  for (int d = 2; d >= 0; --d) {
+    if (!hm[d]) continue;
+    r -= share[d][e][lane];
+#pragma unroll
+    for (int v = 0; v < NB; ++v) dg[v] -= share[d][3 + 3 * e + v][lane];
+  }
+  double* out = stage + (row_start_ijk(M.P, c, i, j, k) - row_start_any(M.P, c0) + (int)hm[0] + (int)hm[1] +
+                         (int)hm[2]) * NB * NB;
+  __stcs(M.res + c * NB + e, r);
+#pragma unroll
+  for (int v = 0; v < NB; ++v) out[e * NB + v] = dg[v];
+  if (!finite(r)) atomicOr(M.status, kStatNonFinite);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ModelArgs* models, ModelArgs single) {
+  pdl_wait();
+  __shared__ Table T;
+  __shared__ unsigned long long bar;
+  __shared__ double self[12][32];
+  __shared__ ClusterShared S;
+  __shared__ union {
+    ClusterCellBuf cell;
+    ClusterFaceBuf face;
+  } buf;
+  extern __shared__ __align__(16) double stage[];   // kClusterStageBlocks blocks
+  unsigned uses = 0;
+  // the model's arguments by value: read once, and no store can alias them
+  const ModelArgs M = models ? models[0] : single;
+  const long long c0 = (long long)blockIdx.x * 32;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long c = c0 + lane;
+  // the cell stage's inputs and the face stage's transmissibility, loaded
+  // while the PVT table is on its way
+  CellIn in{};
+  if (w < 4 && c < M.P.N) load_cell_in<NB>(M, c, in);
+  double Tf = 0.0;
+  {
+    int d, ph;
+    face_task(NB, w, d, ph);
+    if (ph >= 0 && c < M.P.N) Tf = M.trans[d * M.P.N + c];
+  }
+  load_table(T, M.table, bar, uses, M.status);
+  cluster_cell_stage<NB>(M, T, c0, in, buf.cell, S.q, self);
+  __syncthreads();                       // the CTA's own quantities and self[] are complete
+  cluster_arrive();
+  double r = 0.0, dg[NB];
+  cluster_face_stage<NB>(M, c0, Tf, buf.face, S, stage, self, r, dg);   // waits, and arrives again
+  cluster_wait();                        // every share and block is in its CTA's shared memory
+  if (w < NB && c < M.P.N) cluster_assemble<NB>(M, c0, c, w, r, dg, S.share, stage, lane);
+  __syncthreads();
+  // the tile's Jacobian rows, contiguous in val, with coalesced stores
+  const long long b0 = row_start_any(M.P, c0);
+  const long long nv = (row_start_any(M.P, c0 + 32 < M.P.N ? c0 + 32 : M.P.N) - b0) * NB * NB;
+  for (long long q = threadIdx.x; q < nv; q += kClusterThreads) __stcs(M.val + b0 * NB * NB + q, stage[q]);
 }
 
 // ------------------------------------------------------------ ordered launch
@@ -662,6 +1226,50 @@ cudaError_t launch_ordered(int nb, const TileList* lists, OrderedList O, const M
 #undef OCP_ORD
 }
 
+// The one-cluster launch (cfg.ordered 4) of the first model of `models`, or
+// of `single` when models is null: one CTA per 32-cell tile, all of them one
+// cluster.  The model must have at most max_tiles tiles (the largest cluster
+// this device runs, cluster_max_tiles).
+cudaError_t launch_cluster(int nb, const ModelArgs* models, const ModelArgs& single, long long N, int max_tiles,
+                           cudaStream_t s) {
+  const long long nt = (N + 31) / 32;
+  if (nt < 1 || nt > max_tiles || nt > kMaxClusterTiles) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nt);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = kClusterDynSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = (unsigned)nt;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  if (nb == 3) return cudaLaunchKernelEx(&cfg, cluster_kernel<3>, models, single);
+  return cudaLaunchKernelEx(&cfg, cluster_kernel<2>, models, single);
+}
+
+// The largest cluster of cluster_kernel the current device can run (at most
+// kMaxClusterTiles), or 0 if it runs none.  Clusters above 8 CTAs are
+// non-portable and allowed explicitly on the kernel (preload_linearize).
+int cluster_max_tiles(int nb) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kMaxClusterTiles);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = kClusterDynSmem;
+  int n = 0;
+  const cudaError_t e = nb == 3 ? cudaOccupancyMaxPotentialClusterSize(&n, (const void*)cluster_kernel<3>, &cfg)
+                                : cudaOccupancyMaxPotentialClusterSize(&n, (const void*)cluster_kernel<2>, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n < kMaxClusterTiles ? n : kMaxClusterTiles;
+}
+
 // Launches the three stages.  `lists[t]` is the tile list for
 // kTileSizes[t] cells per tile; cfg picks, per stage, the tile size and the
 // grid (CTAs per SM times the SM count, or 0 for one CTA per tile; a
@@ -747,6 +1355,7 @@ cudaError_t launch_single(const ocp_grid* g, double* scratch, const double* u_ne
     lists[t].ntiles = (int)((g->prm.N + kTileSizes[t] - 1) / kTileSizes[t]);
   }
   if (g->cfg.ordered == 0 || g->cfg.ordered == 3) return launch_tiles(g->prm.nb, lists, M, g->cfg, g->sms, s);
+  if (g->cfg.ordered == 4) return launch_cluster(g->prm.nb, nullptr, M, g->prm.N, g->max_cluster, s);
   const long long nmax = (g->prm.N + 31) / 32;       // flags sized for the smallest tiles
   cudaError_t e = cudaMemsetAsync(g->d_sync, 0, sizeof(unsigned) * (1 + 2 * nmax), s);
   if (e != cudaSuccess) return e;
@@ -773,10 +1382,14 @@ cudaError_t preload_linearize(int nb) {
     OCP_LOAD(3, 32) OCP_LOAD(3, 64) OCP_LOAD(3, 128) OCP_LOAD(3, 256)
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, face_split_kernel<3>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, assemble_split_kernel<3>);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cluster_kernel<3>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cluster_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterDynSmem);
   } else {
     OCP_LOAD(2, 32) OCP_LOAD(2, 64) OCP_LOAD(2, 128) OCP_LOAD(2, 256)
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, face_split_kernel<2>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, assemble_split_kernel<2>);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cluster_kernel<2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cluster_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterDynSmem);
   }
 #undef OCP_LOAD
   return e;

@@ -81,8 +81,10 @@ struct LaunchCfg {
   int ctas_per_sm[3];
   int ordered;     // 0: three launches; 1: cell launch + ordered face/assembly launch
                    // (tile size tpb[1], grid ctas_per_sm[1]); 2: one ordered launch;
-                   // 3: three launches, face and assembly split by direction / equation
+                   // 3: three launches, face and assembly split by direction / equation;
+                   // 4: one launch of one thread-block cluster, stages as in 3
 };
+constexpr int kMaxClusterTiles = 16;   // the largest cluster the hardware offers (non-portable)
 constexpr int kNumTileSizes = 4;
 constexpr int kTileSizes[kNumTileSizes] = {32, 64, 128, 256};
 inline int tile_index(int tpb) {
@@ -95,8 +97,10 @@ inline int tile_index(int tpb) {
 // assembly) that still give every SM at least two CTAs, down to 32-cell
 // tiles; a grid too small for that (fewer than 64 cells per SM) takes the
 // face stage split by direction and the assembly by equation, since its
-// time is its warps' FP64 instruction count, not the SMs' throughput.
-inline LaunchCfg default_cfg(long long N, int sms) {
+// time is its warps' FP64 instruction count, not the SMs' throughput, and a
+// grid of at most `max_cluster` 32-cell tiles runs all three stages in one
+// cluster launch.
+inline LaunchCfg default_cfg(long long N, int sms, int max_cluster = 0) {
   LaunchCfg c;
   const long long S = sms > 0 ? sms : 1;
   for (int s = 0; s < 3; ++s) {
@@ -106,6 +110,7 @@ inline LaunchCfg default_cfg(long long N, int sms) {
     c.ctas_per_sm[s] = 0;
   }
   c.ordered = N < 2LL * 32 * S ? 3 : 0;
+  if (N > 0 && (N + 31) / 32 <= max_cluster) c.ordered = 4;
   return c;
 }
 
@@ -140,6 +145,7 @@ struct ocp_grid {
   int64_t scratch_doubles;
   ocp::LaunchCfg cfg;        // launch shape of the linearisation
   int sms;                   // SM count of the device
+  int max_cluster;           // largest one-cluster launch (32-cell tiles) the device runs, 0 if none
   double dx, dy, kz_over_kx; // geometry kept for permeability updates
 };
 
@@ -447,25 +453,31 @@ __device__ __forceinline__ void pvt(const Params& P, const Table& T, double p, d
 // Component amounts per bulk volume, phi S b (eq. 4 in black-oil form), and
 // with DERIV their derivatives with respect to (p, S_w, X).  Used for both
 // time levels, so that an unchanged state gives an exactly zero accumulation.
-template <int NB, bool DERIV>
+// PART 2 computes every component, PART 0 only water and oil, PART 1 only
+// gas (so that the components can be split between warps).
+template <int NB, bool DERIV, int PART = 2>
 __device__ __forceinline__ void masses(const Params& P, const Pvt& f, double p, double sw, double phi_ref,
                                        double* m, double* m_p, double* m_sw, double* m_x) {
   const double phi = phi_ref * fma(P.cr, p - P.p_ref, 1.0);
   const double so = (NB == 3) ? (1.0 - sw - f.sg) : (1.0 - sw);
   const double sob = so * f.bo;
-  m[0] = phi * sw * f.bw;
-  m[1] = phi * sob;
-  if (NB == 3) m[2] = phi * fma(f.sg, f.bg, f.rs * sob);
+  if (PART != 1) {
+    m[0] = phi * sw * f.bw;
+    m[1] = phi * sob;
+  }
+  if (PART != 0 && NB == 3) m[2] = phi * fma(f.sg, f.bg, f.rs * sob);
   if (DERIV) {
     const double phi_p = phi_ref * P.cr;
     const double so_x = -f.sg_x;
-    m_p[0] = fma(phi_p * sw, f.bw, phi * sw * f.bw_p);
-    m_sw[0] = phi * f.bw;
-    m_x[0] = 0.0;
-    m_p[1] = fma(phi_p, sob, phi * so * f.bo_p);
-    m_sw[1] = -phi * f.bo;
-    m_x[1] = phi * fma(so_x, f.bo, so * f.bo_x);
-    if (NB == 3) {
+    if (PART != 1) {
+      m_p[0] = fma(phi_p * sw, f.bw, phi * sw * f.bw_p);
+      m_sw[0] = phi * f.bw;
+      m_x[0] = 0.0;
+      m_p[1] = fma(phi_p, sob, phi * so * f.bo_p);
+      m_sw[1] = -phi * f.bo;
+      m_x[1] = phi * fma(so_x, f.bo, so * f.bo_x);
+    }
+    if (PART != 0 && NB == 3) {
       const double G = fma(f.sg, f.bg, f.rs * sob);
       const double G_p = fma(f.sg, f.bg_p, fma(f.rs_p, sob, f.rs * so * f.bo_p));
       const double G_x = fma(f.sg_x, f.bg, fma(f.rs_x, sob, f.rs * fma(so_x, f.bo, so * f.bo_x)));
@@ -474,6 +486,177 @@ __device__ __forceinline__ void masses(const Params& P, const Pvt& f, double p, 
       m_x[2] = phi * G_x;
     }
   }
+}
+
+// Relative permeabilities of one cell (Corey; Stone II for oil with three
+// phases, SAT module of Sec. 3.2.3) with their derivatives in (S_w, X), and
+// the clamped normalised saturations the capillary pressures use.  `sg` is
+// the cell's gas saturation: X in saturated three-phase cells, else 0.
+struct Kr {
+  double krw, krw_sw, kro, kro_sw, kro_x, krg, krg_x;
+  double s_w, s_w_d, s_g, s_g_d;
+  bool gx;                     // X is S_g (sg_x is 1 there and 0 otherwise)
+};
+
+// The water side (S_w, the oil-water curve) and the gas side (S_g, the
+// oil-gas curve) of the relative permeabilities are independent; rel_perm
+// combines them (so that the two sides can also run in different warps).
+struct KrSide {
+  double s, s_d;               // clamped normalised S_w or S_g and its slope
+  double so_d;                 // slope of the normalised oil saturation of the curve
+  double po, dpo;              // (s_ow or s_og)^n and its derivative
+  double kr, kr_d;             // k_rw or k_rg and its derivative in S_w or S_g
+};
+__device__ __forceinline__ void rel_perm_w(const Params& P, double sw, KrSide& w) {
+  double s_w = (sw - P.swc) * P.inv_w, s_w_d = P.inv_w;
+  clamp01(s_w, s_w_d);
+  double s_ow = (1.0 - sw - P.sorw) * P.inv_w, s_ow_d = -P.inv_w;
+  clamp01(s_ow, s_ow_d);
+  double pw_, dw_, pow_, dow_;
+  cpow(s_w, P.nw, P.sq_w, pw_, dw_);
+  cpow(s_ow, P.now, P.sq_ow, pow_, dow_);
+  w.s = s_w;
+  w.s_d = s_w_d;
+  w.so_d = s_ow_d;
+  w.po = pow_;
+  w.dpo = dow_;
+  w.kr = P.krw_max * pw_;
+  w.kr_d = P.krw_max * dw_ * s_w_d;
+}
+__device__ __forceinline__ void rel_perm_g(const Params& P, double sg, KrSide& g) {
+  double s_g = (sg - P.sgc) * P.inv_g, s_g_d = P.inv_g;
+  clamp01(s_g, s_g_d);
+  double s_og = (1.0 - sg - P.swc - P.sorg) * P.inv_og, s_og_d = -P.inv_og;
+  clamp01(s_og, s_og_d);
+  double pg_, dg_, pog_, dog_;
+  cpow(s_g, P.ng, P.sq_g, pg_, dg_);
+  cpow(s_og, P.nog, P.sq_og, pog_, dog_);
+  g.s = s_g;
+  g.s_d = s_g_d;
+  g.so_d = s_og_d;
+  g.po = pog_;
+  g.dpo = dog_;
+  g.kr = P.krg_max * pg_;
+  g.kr_d = P.krg_max * dg_ * s_g_d;
+}
+// k_ro (Stone II with three phases, the oil-water curve with two) from the
+// two sides; the sums are explicitly rounded so that they never take in a
+// product from the side computations, wherever those ran.
+template <int NB>
+__device__ __forceinline__ void rel_perm_combine(const Params& P, const KrSide& w, const KrSide& g, int flag,
+                                                 Kr& k) {
+  double kro, kro_sw, kro_sg = 0.0, krg = 0.0, krg_sg = 0.0, s_g = 0.0, s_g_d = 0.0;
+  if (NB == 3) {
+    krg = g.kr;
+    krg_sg = g.kr_d;
+    s_g = g.s;
+    s_g_d = g.s_d;
+    // k_ro = kc [(k_row/kc + k_rw)(k_rog/kc + k_rg) - (k_rw + k_rg)], k_row/kc = s_ow^n
+    const double A = __dadd_rn(w.po, w.kr);
+    const double A_sw = fma(w.dpo, w.so_d, w.kr_d);
+    const double B = __dadd_rn(g.po, krg);
+    const double B_sg = fma(g.dpo, g.so_d, krg_sg);
+    kro = P.kc * fma(A, B, -__dadd_rn(w.kr, krg));
+    kro_sw = P.kc * fma(A_sw, B, -w.kr_d);
+    kro_sg = P.kc * fma(A, B_sg, -krg_sg);
+    if (!nonneg(kro)) { kro = 0.0; kro_sw = 0.0; kro_sg = 0.0; }
+  } else {
+    kro = P.kc * w.po;
+    kro_sw = P.kc * w.dpo * w.so_d;
+  }
+  const bool gx = (NB == 3) && (flag == 0);
+  k.krw = w.kr;
+  k.krw_sw = w.kr_d;
+  k.kro = kro;
+  k.kro_sw = kro_sw;
+  k.kro_x = gx ? kro_sg : 0.0;
+  k.krg = krg;
+  k.krg_x = gx ? krg_sg : 0.0;
+  k.s_w = w.s;
+  k.s_w_d = w.s_d;
+  k.s_g = s_g;
+  k.s_g_d = s_g_d;
+  k.gx = gx;
+}
+
+template <int NB>
+__device__ __forceinline__ void rel_perm(const Params& P, double sw, double sg, int flag, Kr& k) {
+  KrSide w, g{};
+  rel_perm_w(P, sw, w);
+  if (NB == 3) rel_perm_g(P, sg, g);
+  rel_perm_combine<NB>(P, w, g, flag, k);
+}
+
+// Capillary pressures: p_w = p - Pc_ow(S_w), p_g = p + Pc_go(S_g).
+template <int NB>
+__device__ __forceinline__ void cap_pressure(const Params& P, double p, const Kr& k, CellQ& q) {
+  const double omw = 1.0 - k.s_w;
+  q.p = p;
+  q.pw = p - P.pcow_max * (omw * omw);
+  q.dpw_sw = P.pcow2 * omw * k.s_w_d;
+  if (NB == 3) {
+    q.pg = p + P.pcgo_max * (k.s_g * k.s_g);
+    q.dpg_x = k.gx ? P.pcgo2 * k.s_g * k.s_g_d : 0.0;
+  }
+}
+
+// Phase densities and mobilities lambda = k_r b / mu with their derivatives:
+// water and gas (WG), oil (O), or all.
+template <int NB, bool WG = true, bool O = true>
+__device__ __forceinline__ void dens_mob(const Params& P, const Pvt& f, const Kr& k, CellQ& q) {
+  if (WG) {
+    q.rw = f.bw * P.rho_wsc;
+    q.rw_p = P.rw_p;
+    if (NB == 3) {
+      q.rg = f.bg * P.cg;
+      q.rg_p = f.bg_p * P.cg;
+    }
+    const double bmw = f.bw * P.imu_w;
+    q.lw = k.krw * bmw;
+    q.lw_p = k.krw * P.bw_p_imu;
+    q.lw_sw = k.krw_sw * bmw;
+    if (NB == 3) {
+      const double bmg = f.bg * f.img;
+      q.lg = k.krg * bmg;
+      q.lg_p = k.krg * fma(f.bg_p, f.img, f.bg * f.img_p);
+      q.lg_x = k.krg_x * bmg;
+      q.rs = f.rs; q.rs_p = f.rs_p; q.rs_x = f.rs_x;
+    }
+  }
+  if (!O) return;
+  const double ro0 = fma(f.rs, P.cg, P.rho_osc);
+  q.ro = ro0 * f.bo;
+  q.ro_p = fma(P.cg * f.rs_p, f.bo, ro0 * f.bo_p);
+  q.ro_x = fma(P.cg * f.rs_x, f.bo, ro0 * f.bo_x);
+  const double bmo = f.bo * f.imo;
+  const double bmo_p = fma(f.bo_p, f.imo, f.bo * f.imo_p);
+  const double bmo_x = fma(f.bo_x, f.imo, f.bo * f.imo_x);
+  q.lo = k.kro * bmo;
+  q.lo_p = k.kro * bmo_p;
+  q.lo_sw = k.kro_sw * bmo;
+  q.lo_x = fma(k.kro_x, bmo, k.kro * bmo_x);
+}
+
+// Total mobility sum k_r / mu and the injected phases' b (injector cells;
+// zero elsewhere).
+template <int NB>
+__device__ __forceinline__ void total_mob(const Params& P, const Pvt& f, const Kr& k, bool injector,
+                                          CellAux& a) {
+  a.mob = a.mob_p = a.mob_sw = a.mob_x = 0.0;
+  if (!injector) {
+  } else if (NB == 3) {
+    a.mob = fma(k.krw, P.imu_w, fma(k.kro, f.imo, k.krg * f.img));
+    a.mob_p = fma(k.kro, f.imo_p, k.krg * f.img_p);
+    a.mob_sw = fma(k.krw_sw, P.imu_w, k.kro_sw * f.imo);
+    a.mob_x = fma(k.kro_x, f.imo, fma(k.kro, f.imo_x, k.krg_x * f.img));
+    a.bg = f.bg; a.bg_p = f.bg_p;
+  } else {
+    a.mob = fma(k.krw, P.imu_w, k.kro * f.imo);
+    a.mob_p = k.kro * f.imo_p;
+    a.mob_sw = fma(k.krw_sw, P.imu_w, k.kro_sw * f.imo);
+    a.mob_x = 0.0;
+  }
+  a.bw = f.bw; a.bw_p = f.bw_p;
 }
 
 // PVT, rock, Corey / Stone II, capillary pressure, densities and mobilities
@@ -486,107 +669,13 @@ __device__ __forceinline__ void cell_quantities(const Params& P, const Table& T,
                                                 CellAux& a, bool injector = true) {
   Pvt f;
   pvt<NB, true>(P, T, p, x, flag, f);
-  const double sg = f.sg;
-
-  // relative permeabilities (Corey; Stone II for oil with three phases)
-  double s_w = (sw - P.swc) * P.inv_w, s_w_d = P.inv_w;
-  clamp01(s_w, s_w_d);
-  double s_ow = (1.0 - sw - P.sorw) * P.inv_w, s_ow_d = -P.inv_w;
-  clamp01(s_ow, s_ow_d);
-  double pw_, dw_, pow_, dow_;
-  cpow(s_w, P.nw, P.sq_w, pw_, dw_);
-  cpow(s_ow, P.now, P.sq_ow, pow_, dow_);
-  const double krw = P.krw_max * pw_;
-  const double krw_sw = P.krw_max * dw_ * s_w_d;
-  double kro, kro_sw, kro_sg = 0.0, krg = 0.0, krg_sg = 0.0, s_g = 0.0, s_g_d = 0.0;
-  if (NB == 3) {
-    s_g = (sg - P.sgc) * P.inv_g;
-    s_g_d = P.inv_g;
-    clamp01(s_g, s_g_d);
-    double s_og = (1.0 - sg - P.swc - P.sorg) * P.inv_og, s_og_d = -P.inv_og;
-    clamp01(s_og, s_og_d);
-    double pg_, dg_, pog_, dog_;
-    cpow(s_g, P.ng, P.sq_g, pg_, dg_);
-    cpow(s_og, P.nog, P.sq_og, pog_, dog_);
-    krg = P.krg_max * pg_;
-    krg_sg = P.krg_max * dg_ * s_g_d;
-    // k_ro = kc [(k_row/kc + k_rw)(k_rog/kc + k_rg) - (k_rw + k_rg)], k_row/kc = s_ow^n
-    const double A = pow_ + krw;
-    const double A_sw = fma(dow_, s_ow_d, krw_sw);
-    const double B = pog_ + krg;
-    const double B_sg = fma(dog_, s_og_d, krg_sg);
-    kro = P.kc * fma(A, B, -(krw + krg));
-    kro_sw = P.kc * fma(A_sw, B, -krw_sw);
-    kro_sg = P.kc * fma(A, B_sg, -krg_sg);
-    if (!nonneg(kro)) { kro = 0.0; kro_sw = 0.0; kro_sg = 0.0; }
-  } else {
-    kro = P.kc * pow_;
-    kro_sw = P.kc * dow_ * s_ow_d;
-  }
-  // X is S_g only in saturated cells (sg_x is 1 there and 0 otherwise)
-  const bool gx = (NB == 3) && (flag == 0);
-  const double kro_x = gx ? kro_sg : 0.0;
-  const double krg_x = gx ? krg_sg : 0.0;
-
-  // capillary pressures: p_w = p - Pc_ow(S_w), p_g = p + Pc_go(S_g)
-  const double omw = 1.0 - s_w;
-  q.p = p;
-  q.pw = p - P.pcow_max * (omw * omw);
-  q.dpw_sw = P.pcow2 * omw * s_w_d;
-  if (NB == 3) {
-    q.pg = p + P.pcgo_max * (s_g * s_g);
-    q.dpg_x = gx ? P.pcgo2 * s_g * s_g_d : 0.0;
-  }
-
-  // densities
-  q.rw = f.bw * P.rho_wsc;
-  q.rw_p = P.rw_p;
-  const double ro0 = fma(f.rs, P.cg, P.rho_osc);
-  q.ro = ro0 * f.bo;
-  q.ro_p = fma(P.cg * f.rs_p, f.bo, ro0 * f.bo_p);
-  q.ro_x = fma(P.cg * f.rs_x, f.bo, ro0 * f.bo_x);
-  if (NB == 3) {
-    q.rg = f.bg * P.cg;
-    q.rg_p = f.bg_p * P.cg;
-  }
-
-  // mobilities lambda = k_r * b / mu
-  const double bmw = f.bw * P.imu_w;
-  q.lw = krw * bmw;
-  q.lw_p = krw * P.bw_p_imu;
-  q.lw_sw = krw_sw * bmw;
-  const double bmo = f.bo * f.imo;
-  const double bmo_p = fma(f.bo_p, f.imo, f.bo * f.imo_p);
-  const double bmo_x = fma(f.bo_x, f.imo, f.bo * f.imo_x);
-  q.lo = kro * bmo;
-  q.lo_p = kro * bmo_p;
-  q.lo_sw = kro_sw * bmo;
-  q.lo_x = fma(kro_x, bmo, kro * bmo_x);
-  if (NB == 3) {
-    const double bmg = f.bg * f.img;
-    q.lg = krg * bmg;
-    q.lg_p = krg * fma(f.bg_p, f.img, f.bg * f.img_p);
-    q.lg_x = krg_x * bmg;
-    q.rs = f.rs; q.rs_p = f.rs_p; q.rs_x = f.rs_x;
-  }
-
+  Kr k;
+  rel_perm<NB>(P, sw, f.sg, flag, k);
+  cap_pressure<NB>(P, p, k, q);
+  dens_mob<NB>(P, f, k, q);
   if (AUX) {
     masses<NB, true>(P, f, p, sw, phi_ref, a.m, a.m_p, a.m_sw, a.m_x);
-    a.mob = a.mob_p = a.mob_sw = a.mob_x = 0.0;
-    if (!injector) {
-    } else if (NB == 3) {
-      a.mob = fma(krw, P.imu_w, fma(kro, f.imo, krg * f.img));
-      a.mob_p = fma(kro, f.imo_p, krg * f.img_p);
-      a.mob_sw = fma(krw_sw, P.imu_w, kro_sw * f.imo);
-      a.mob_x = fma(kro_x, f.imo, fma(kro, f.imo_x, krg_x * f.img));
-      a.bg = f.bg; a.bg_p = f.bg_p;
-    } else {
-      a.mob = fma(krw, P.imu_w, kro * f.imo);
-      a.mob_p = kro * f.imo_p;
-      a.mob_sw = fma(krw_sw, P.imu_w, kro_sw * f.imo);
-      a.mob_x = 0.0;
-    }
-    a.bw = f.bw; a.bw_p = f.bw_p;
+    total_mob<NB>(P, f, k, injector, a);
   }
 }
 
@@ -678,43 +767,98 @@ struct FaceOut {
   double dj[NB][3];   // dF_e / du_j[v]
 };
 
+// The three phases across one face (water, oil, gas) as separate calls, so
+// that a face can also be computed one phase per warp; face_terms chains
+// them.  a is cell i, b its + neighbour j.
+template <int NB, bool GRAV>
+__device__ __forceinline__ void water_flux(double T, double hz, const CellQ& a, const CellQ& b, double& F,
+                                           double (&di)[3], double (&dj)[3], bool& up) {
+  // water: p_w = p - Pc_ow(S_w); rho_w and lambda_w depend on p and S_w
+  phase_flux<GRAV, true, false, false, true, false>(T, hz, a.pw, b.pw, a.dpw_sw, b.dpw_sw, a.rw, b.rw, a.rw_p,
+                                                     b.rw_p, 0.0, 0.0, a.lw, b.lw, a.lw_p, b.lw_p, a.lw_sw,
+                                                     b.lw_sw, 0.0, 0.0, F, di, dj, up);
+}
+template <int NB, bool GRAV>
+__device__ __forceinline__ void oil_flux(double T, double hz, const CellQ& a, const CellQ& b, double& F,
+                                         double (&di)[3], double (&dj)[3], bool& up) {
+  // oil: p_o = p; rho_o and lambda_o depend on X only with three phases
+  phase_flux<GRAV, false, false, NB == 3, true, NB == 3>(T, hz, a.p, b.p, 0.0, 0.0, a.ro, b.ro, a.ro_p, b.ro_p,
+                                                          a.ro_x, b.ro_x, a.lo, b.lo, a.lo_p, b.lo_p, a.lo_sw,
+                                                          b.lo_sw, a.lo_x, b.lo_x, F, di, dj, up);
+}
+template <int NB, bool GRAV>
+__device__ __forceinline__ void gas_flux(double T, double hz, const CellQ& a, const CellQ& b, double& F,
+                                         double (&di)[3], double (&dj)[3], bool& up) {
+  // gas: p_g = p + Pc_go(S_g); rho_g depends on p, lambda_g on p and X
+  phase_flux<GRAV, false, true, false, false, true>(T, hz, a.pg, b.pg, a.dpg_x, b.dpg_x, a.rg, b.rg, a.rg_p,
+                                                     b.rg_p, 0.0, 0.0, a.lg, b.lg, a.lg_p, b.lg_p, 0.0, 0.0,
+                                                     a.lg_x, b.lg_x, F, di, dj, up);
+}
+// The gas component: free gas plus the gas dissolved in the upstream oil
+// (Fo, di_o, dj_o, up_o the oil phase; Fg, dg_i, dg_j the gas phase).
+__device__ __forceinline__ void gas_component(const CellQ& a, const CellQ& b, bool up_o, double Fo,
+                                              const double (&di_o)[3], const double (&dj_o)[3], double Fg,
+                                              const double (&dg_i)[3], const double (&dg_j)[3], double& F,
+                                              double (&di)[3], double (&dj)[3]) {
+  const double rsu = sel(up_o, a.rs, b.rs);
+  F = fma(rsu, Fo, Fg);
+  const double frp = Fo * sel(up_o, a.rs_p, b.rs_p);
+  const double frx = Fo * sel(up_o, a.rs_x, b.rs_x);
+  di[0] = fma(rsu, di_o[0], dg_i[0]) + sel(up_o, frp, 0.0);
+  dj[0] = fma(rsu, dj_o[0], dg_j[0]) + sel(up_o, 0.0, frp);
+  di[1] = rsu * di_o[1];
+  dj[1] = rsu * dj_o[1];
+  di[2] = fma(rsu, di_o[2], dg_i[2]) + sel(up_o, frx, 0.0);
+  dj[2] = fma(rsu, dj_o[2], dg_j[2]) + sel(up_o, 0.0, frx);
+}
+
 template <int NB, bool GRAV>
 __device__ __forceinline__ void face_terms(double T, double hz, const CellQ& a, const CellQ& b,
                                            FaceOut<NB>& o) {
   bool up_w, up_o;
-  // water: p_w = p - Pc_ow(S_w); rho_w and lambda_w depend on p and S_w
-  phase_flux<GRAV, true, false, false, true, false>(T, hz, a.pw, b.pw, a.dpw_sw, b.dpw_sw, a.rw, b.rw,
-                                                     a.rw_p, b.rw_p, 0.0, 0.0, a.lw, b.lw, a.lw_p, b.lw_p,
-                                                     a.lw_sw, b.lw_sw, 0.0, 0.0, o.F[0], o.di[0], o.dj[0],
-                                                     up_w);
-  // oil: p_o = p; rho_o and lambda_o depend on X only with three phases
-  phase_flux<GRAV, false, false, NB == 3, true, NB == 3>(T, hz, a.p, b.p, 0.0, 0.0, a.ro, b.ro, a.ro_p,
-                                                          b.ro_p, a.ro_x, b.ro_x, a.lo, b.lo, a.lo_p, b.lo_p,
-                                                          a.lo_sw, b.lo_sw, a.lo_x, b.lo_x, o.F[1], o.di[1],
-                                                          o.dj[1], up_o);
+  water_flux<NB, GRAV>(T, hz, a, b, o.F[0], o.di[0], o.dj[0], up_w);
+  oil_flux<NB, GRAV>(T, hz, a, b, o.F[1], o.di[1], o.dj[1], up_o);
   if (NB == 3) {
     double Fg, dg_i[3], dg_j[3];
     bool up_g;
-    // gas: p_g = p + Pc_go(S_g); rho_g depends on p, lambda_g on p and X
-    phase_flux<GRAV, false, true, false, false, true>(T, hz, a.pg, b.pg, a.dpg_x, b.dpg_x, a.rg, b.rg,
-                                                       a.rg_p, b.rg_p, 0.0, 0.0, a.lg, b.lg, a.lg_p, b.lg_p,
-                                                       0.0, 0.0, a.lg_x, b.lg_x, Fg, dg_i, dg_j, up_g);
-    // gas component: free gas plus gas dissolved in the upstream oil
-    const double rsu = sel(up_o, a.rs, b.rs);
-    const double Fo = o.F[1];
-    o.F[NB - 1] = fma(rsu, Fo, Fg);
-    const double frp = Fo * sel(up_o, a.rs_p, b.rs_p);
-    const double frx = Fo * sel(up_o, a.rs_x, b.rs_x);
-    o.di[NB - 1][0] = fma(rsu, o.di[1][0], dg_i[0]) + sel(up_o, frp, 0.0);
-    o.dj[NB - 1][0] = fma(rsu, o.dj[1][0], dg_j[0]) + sel(up_o, 0.0, frp);
-    o.di[NB - 1][1] = rsu * o.di[1][1];
-    o.dj[NB - 1][1] = rsu * o.dj[1][1];
-    o.di[NB - 1][2] = fma(rsu, o.di[1][2], dg_i[2]) + sel(up_o, frx, 0.0);
-    o.dj[NB - 1][2] = fma(rsu, o.dj[1][2], dg_j[2]) + sel(up_o, 0.0, frx);
+    gas_flux<NB, GRAV>(T, hz, a, b, Fg, dg_i, dg_j, up_g);
+    gas_component(a, b, up_o, o.F[1], o.di[1], o.dj[1], Fg, dg_i, dg_j, o.F[NB - 1], o.di[NB - 1],
+                  o.dj[NB - 1]);
   }
 }
 
 // ---------------------------------------------------------------- wells
+// Producer terms q_a = WI lambda_a (p_bh - p) by phase (g = p_bh - p < 0):
+// well_source chains them; they can also run in different warps.
+__device__ __forceinline__ void well_prod_water(const Perf& w, const CellQ& q, double g, double& src,
+                                                double (&d)[3]) {
+  src = w.wi * q.lw * g;
+  d[0] = w.wi * fma(q.lw_p, g, -q.lw);
+  d[1] = w.wi * q.lw_sw * g;
+}
+__device__ __forceinline__ void well_prod_oil(const Perf& w, const CellQ& q, double g, double& src,
+                                              double (&d)[3]) {
+  src = w.wi * q.lo * g;
+  d[0] = w.wi * fma(q.lo_p, g, -q.lo);
+  d[1] = w.wi * q.lo_sw * g;
+  d[2] = w.wi * q.lo_x * g;
+}
+// The free-gas rate and its p and X derivatives.
+__device__ __forceinline__ void well_prod_gas_free(const Perf& w, const CellQ& q, double g, double (&qg)[3]) {
+  qg[0] = w.wi * q.lg * g;
+  qg[1] = w.wi * fma(q.lg_p, g, -q.lg);
+  qg[2] = w.wi * q.lg_x * g;
+}
+// The gas component: the free gas plus the gas dissolved in the produced oil
+// (src_o, d_o the oil row).
+__device__ __forceinline__ void well_prod_gas(const CellQ& q, double src_o, const double (&d_o)[3],
+                                              const double (&qg)[3], double& src, double (&d)[3]) {
+  src = fma(q.rs, src_o, qg[0]);
+  d[0] = fma(q.rs, d_o[0], fma(q.rs_p, src_o, qg[1]));
+  d[1] = q.rs * d_o[1];
+  d[2] = fma(q.rs, d_o[2], fma(q.rs_x, src_o, qg[2]));
+}
+
 // Source of every component at a perforated cell (positive into the
 // reservoir) and its derivatives (AllWells, Sec. 3.2.4).
 template <int NB>
@@ -728,22 +872,12 @@ __device__ __forceinline__ void well_source(const Perf& w, const CellQ& q, const
     const double drive = q.p - w.p_bh;
     if (!positive(drive)) return;
     const double g = w.p_bh - q.p;   // negative
-    // q_a = WI lambda_a (p_bh - p)
-    src[0] = w.wi * q.lw * g;
-    d[0][0] = w.wi * fma(q.lw_p, g, -q.lw);
-    d[0][1] = w.wi * q.lw_sw * g;
-    src[1] = w.wi * q.lo * g;
-    d[1][0] = w.wi * fma(q.lo_p, g, -q.lo);
-    d[1][1] = w.wi * q.lo_sw * g;
-    d[1][2] = w.wi * q.lo_x * g;
+    well_prod_water(w, q, g, src[0], d[0]);
+    well_prod_oil(w, q, g, src[1], d[1]);
     if (NB == 3) {
-      const double qg = w.wi * q.lg * g;
-      const double qg_p = w.wi * fma(q.lg_p, g, -q.lg);
-      const double qg_x = w.wi * q.lg_x * g;
-      src[2] = fma(q.rs, src[1], qg);
-      d[2][0] = fma(q.rs, d[1][0], fma(q.rs_p, src[1], qg_p));
-      d[2][1] = q.rs * d[1][1];
-      d[2][2] = fma(q.rs, d[1][2], fma(q.rs_x, src[1], qg_x));
+      double qg[3];
+      well_prod_gas_free(w, q, g, qg);
+      well_prod_gas(q, src[1], d[1], qg, src[2], d[2]);
     }
   } else {
     const double drive = w.p_bh - q.p;

@@ -29,7 +29,7 @@ EXPORTS = ["ocp_grid_create", "ocp_grid_destroy", "ocp_grid_info", "ocp_bsr_patt
            "ocp_linearize_noalloc", "ocp_probe_fp64", "ocp_batch_create", "ocp_batch_destroy",
            "ocp_batch_set_io", "ocp_batch_linearize", "ocp_batch_graph_launch", "ocp_batch_tune",
            "ocp_batch_set_shape", "ocp_batch_get_shape", "ocp_batch_get_status", "ocp_grid_set_shape",
-           "ocp_grid_get_shape",
+           "ocp_grid_get_shape", "ocp_grid_cluster_tiles",
            "ocp_solver_work_doubles", "ocp_bicgstab", "ocp_newton_update", "ocp_well_rates_vjp",
            "ocp_grid_update_perm", "ocp_coupling_work_ints", "ocp_coupling_components", "ocp_linearize_wells",
            "ocp_bicgstab_wells", "ocp_well_update", "ocp_residual_norms", "ocp_linearize_pn", "ocp_pn_update",
@@ -135,6 +135,7 @@ def load(build_if_missing: bool = False):
     lib.ocp_batch_get_status.argtypes = [vp, vp]
     lib.ocp_grid_set_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
     lib.ocp_grid_get_shape.argtypes = [vp, ctypes.POINTER(_Shape)]
+    lib.ocp_grid_cluster_tiles.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.ocp_solver_work_doubles.argtypes = [vp]
     lib.ocp_solver_work_doubles.restype = ctypes.c_int64
     lib.ocp_bicgstab.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp,
@@ -551,6 +552,13 @@ class Grid:
         sh = _Shape()
         _check(load().ocp_grid_get_shape(self._h, ctypes.byref(sh)))
         return shape_to_dict(sh)
+
+    def cluster_tiles(self):
+        """Largest grid, in 32-cell tiles, that the one-cluster launch
+        (``ordered = 4``) takes on this grid's device; 0 if none."""
+        n = ctypes.c_int()
+        _check(load().ocp_grid_cluster_tiles(self._h, ctypes.byref(n)))
+        return n.value
 
 
 def shape_to_dict(sh):

@@ -111,7 +111,7 @@ def test_tuner_returns_a_valid_shape_and_keeps_results():
     batch.set_io(ios)
     best = batch.tune(1.0, reps=2)
     assert all(t in (32, 64, 128, 256) for t in best["cells_per_tile"])
-    assert all(0 <= c <= 16 for c in best["ctas_per_sm"]) and best["ordered"] in (0, 1, 2, 3)
+    assert all(0 <= c <= 16 for c in best["ctas_per_sm"]) and best["ordered"] in (0, 1, 2, 3)   # not 4: 6 models
     assert batch.get_shape() == best
     batch.linearize(1.0, graph=True)
     torch.cuda.synchronize()
@@ -135,5 +135,40 @@ def test_batch_status_and_errors():
         O.Batch([grids[0], O.Grid(g2)])            # mixed block sizes
     with pytest.raises(O.OcpError):
         batch.set_shape(dict(cells_per_tile=[48, 256, 256], ctas_per_sm=[0, 0, 0]))
-    with pytest.raises(O.OcpError):
+    with pytest.raises(O.OcpError):                 # one cluster takes one grid only
         batch.set_shape(dict(cells_per_tile=[64, 256, 256], ctas_per_sm=[0, 0, 0], ordered=4))
+    with pytest.raises(O.OcpError):
+        batch.set_shape(dict(cells_per_tile=[64, 256, 256], ctas_per_sm=[0, 0, 0], ordered=5))
+
+
+def test_one_grid_batch_runs_as_one_cluster():
+    """A batch of one small grid starts in the one-cluster launch; set, tuned,
+    or replayed as a graph across dt changes, it gives the bits of the grid's
+    own three plain launches."""
+    O = ocp()
+    g, s = W.tiny(10, 10, 3, nphase=3, seed=120, frac_unsat=0.3)
+    grid = O.Grid(g)
+    un, fn, uo, fo = dev_state(s)
+    io = dict(u_new=un, flag_new=fn, u_old=uo, flag_old=fo,
+              residual=torch.empty(grid.nb * grid.N, dtype=torch.float64, device="cuda"),
+              bsr_val=torch.empty(grid.nnzb * grid.nb ** 2, dtype=torch.float64, device="cuda"),
+              face_flux=torch.empty(3 * grid.nb * grid.N, dtype=torch.float64, device="cuda"))
+    batch = O.Batch([grid])
+    batch.set_io([io])
+    assert batch.get_shape()["ordered"] == 4
+    grid.set_shape(dict(cells_per_tile=[128, 128, 256], ctas_per_sm=[0, 0, 0], ordered=0))
+    for dt in (1.0, 0.25, 0.25, 3.0):
+        r, v, f = (t.clone() for t in grid.linearize(un, fn, uo, fo, dt, want_face_flux=True))
+        for graph in (False, True):
+            for k in ("residual", "bsr_val", "face_flux"):
+                io[k].fill_(np.nan)
+            batch.linearize(dt, graph=graph)
+            torch.cuda.synchronize()
+            assert batch.status() == 0
+            assert same_bits(io["residual"], r) and same_bits(io["bsr_val"], v) and same_bits(io["face_flux"], f)
+    best = batch.tune(1.0, reps=2)
+    assert best["ordered"] in (0, 1, 2, 3, 4)
+    batch.linearize(1.0)
+    torch.cuda.synchronize()
+    r, v, f = grid.linearize(un, fn, uo, fo, 1.0, want_face_flux=True)
+    assert same_bits(io["residual"], r) and same_bits(io["bsr_val"], v)

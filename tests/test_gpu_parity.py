@@ -88,13 +88,15 @@ def test_linearize_is_deterministic():
 
 
 @pytest.mark.parametrize("nphase,shape", [(3, (13, 11, 7)), (3, (100, 3, 2)), (2, (9, 30, 5)), (3, (1, 1, 1)),
-                                          (3, (40, 40, 3))])
+                                          (3, (40, 40, 3)), (3, (10, 10, 3)), (2, (8, 8, 5)), (3, (16, 8, 4)),
+                                          (3, (7, 5, 9))])
 def test_launch_shapes_are_bitwise_identical(nphase, shape):
     """Every launch shape of one grid -- tile sizes 32 to 256, one CTA per
     tile or persistent grids, three launches or the ordered launches (face
     stage and assembly in one persistent launch after the cell stage, or
-    everything in one), or faces and assembly split by direction and equation
-    -- gives the same bits, and those match the oracle."""
+    everything in one), faces and assembly split by direction and equation,
+    and for grids of at most 16 tiles of 32 cells the one-cluster launch --
+    gives the same bits, and those match the oracle."""
     O = ocp()
     g, s = W.tiny(*shape, nphase=nphase, seed=sum(shape) + 7, frac_unsat=0.3 if nphase == 3 else 0.0)
     grid = O.Grid(g)
@@ -112,6 +114,15 @@ def test_launch_shapes_are_bitwise_identical(nphase, shape):
     # face and assembly split by direction and equation
     shapes.append(dict(cells_per_tile=[32, 32, 32], ctas_per_sm=[0, 0, 0], ordered=3))
     shapes.append(dict(cells_per_tile=[128, 32, 32], ctas_per_sm=[2, 1, 3], ordered=3))
+    # everything in one thread-block cluster: GB300 runs clusters of 16 CTAs
+    tiles = (g.N + 31) // 32
+    assert grid.cluster_tiles() == 16
+    if tiles <= 16:
+        assert grid.get_shape()["ordered"] == 4            # the default for grids that fit
+        shapes.append(dict(cells_per_tile=[32, 32, 32], ctas_per_sm=[0, 0, 0], ordered=4))
+    else:
+        with pytest.raises(O.OcpError):
+            grid.set_shape(dict(cells_per_tile=[32, 32, 32], ctas_per_sm=[0, 0, 0], ordered=4))
     for sh in shapes:
         grid.set_shape(sh)
         got = gpu_linearize(grid, s)
