@@ -72,6 +72,23 @@ __device__ __forceinline__ void load_q(const double* s, long long N, long long c
   for (int i = 0; i < kQ; ++i) f[i] = q_used<NB>(i) ? lds<COH>(s + i * N + c) : 0.0;
 }
 
+// Drops from L2, without writing them back to DRAM, the 128-byte lines of
+// scratch fields [f0, f1) that hold only cells [c0, c0 + TPB) (clamped to
+// N): called once every reader of those cells' scratch is done, so that dead
+// scratch costs no DRAM write.  Lines shared with other cells are left
+// alone.  All threads of the CTA call it, after a barrier.
+template <int TPB>
+__device__ __forceinline__ void discard_scratch(const double* s, long long N, long long c0, int f0, int f1) {
+  constexpr int kPer = TPB / 16 >= 8 ? TPB / 8 : 8;      // power of two above the lines a range can touch
+  const long long c1 = c0 + TPB < N ? c0 + TPB : N;
+  for (int k = threadIdx.x; k < (f1 - f0) * kPer; k += blockDim.x) {
+    const int f = f0 + k / kPer, j = k % kPer;
+    const uintptr_t a = (uintptr_t)(s + f * N + c0), b = (uintptr_t)(s + f * N + c1);
+    const uintptr_t line = ((a + 127) & ~(uintptr_t)127) + 128 * (uintptr_t)j;
+    if (line + 128 <= b) asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
+  }
+}
+
 template <int NB>
 __device__ __forceinline__ void cell_body(const ModelArgs& M, const Table& T, long long c) {
   const Params& P = M.P;
@@ -1095,6 +1112,8 @@ __global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) ordered_kern
   __shared__ int s_model, s_kind, s_stop;
   unsigned uses = 0;
   int cur = -1;
+  int dead = -1;                            // model and first cell of the tile whose scratch died
+  long long dead_c0 = 0;                    // in the previous face item
   for (;;) {
     if (threadIdx.x == 0) {
       const long long item = (long long)atomicAdd(O.counter, 1u);
@@ -1123,6 +1142,12 @@ __global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) ordered_kern
     }
     __syncthreads();
     if (s_stop) break;
+    if (dead >= 0) {                          // every thread is past the previous item
+      const ModelArgs& D = O.models ? O.models[O.order[dead]] : single;
+      discard_scratch<TPB>(D.scr, D.P.N, dead_c0, 0, kSelf + 12);
+      discard_scratch<TPB>(D.scr, D.P.N, dead_c0, kInc, kInc + 36);
+      dead = -1;
+    }
     const int mo = s_model, kind = s_kind;
     const long long t = s_tile;
     __syncthreads();                          // everyone has read the item before it is overwritten
@@ -1160,6 +1185,18 @@ __global__ void __launch_bounds__(TPB, (NB == 3 ? 384 : 512) / TPB) ordered_kern
       wait_tiles<TPB>(O.flag_face + fbase, lo, hi, N, t, M.status);
     }
     if (c < N) assemble_rows<NB, true>(M, c, r, dg);
+    // The tile's scratch is now dead: its shares were just read, its own
+    // terms in its face stage, and its cell quantities by its own face stage
+    // and by the face stages of the tiles holding its cells' - neighbours,
+    // which the wait above saw finish.  Its L2 lines are dropped after the
+    // next item's barrier (every thread is past the assembly then).
+    dead = mo;
+    dead_c0 = c0;
+  }
+  if (dead >= 0) {
+    const ModelArgs& D = O.models ? O.models[O.order[dead]] : single;
+    discard_scratch<TPB>(D.scr, D.P.N, dead_c0, 0, kSelf + 12);
+    discard_scratch<TPB>(D.scr, D.P.N, dead_c0, kInc, kInc + 36);
   }
 }
 
