@@ -58,11 +58,11 @@ STORED = {
              "dram_bytes": 104.04e6, "fp64_inst_per_cell": 63.84, "fp64_warp_inst_per_cell": 2.0041},
     # FP64 counts: the three stage kernels' sum (the one-launch ordered kernel
     # executes 372.54 / 12.0007).  DRAM bytes per call by launch mode
-    # ("ordered" of the launch shape): 0 with 128/128/256-cell tiles, 2 with
-    # 64-cell tiles
-    "linearize": {"sources": ["linearize.cu", "ocp_internal.cuh"], "sha16": "2429d2e2e1b5ec31",
+    # ("ordered" of the launch shape): 0 with 128/128/256-cell tiles, 1 and 2
+    # with 64-cell tiles
+    "linearize": {"sources": ["linearize.cu", "ocp_internal.cuh"], "sha16": "3b5f85b96bae2ac7",
                   "fp64_inst_per_cell": 370.54, "fp64_warp_inst_per_cell": 11.9382,
-                  "dram_bytes": {"0": 327.00e6, "2": 217.95e6}},
+                  "dram_bytes": {"0": 326.46e6, "1": 204.12e6, "2": 120.59e6}},
     "vjp": {"sources": ["spmv_adjoint.cu", "ocp_internal.cuh"], "sha16": "2ba72b24cb9f1a7a",
             "fp64_inst_per_cell": 177.19, "fp64_warp_inst_per_cell": 5.5739, "dram_bytes": 147.84e6},
 }
@@ -664,12 +664,18 @@ def lin_line(N, nnzb, ms, shape, shape_src, hbm_peak):
     residual, Jacobian) against the copy rate, and FP64 instructions
     against the FP64 pipe's rate (ncu counts stored with their sources)."""
     alg = 106.0 * N + 72.0 * nnzb
-    traffic = (stored("linearize", "dram_bytes") or {}).get(str(shape["ordered"]))
+    by_mode = stored("linearize", "dram_bytes") or {}
+    traffic = by_mode.get(str(shape["ordered"]))
     return {"mcells": N / (ms * 1e-3) / 1e6, "ms": ms, "launch_shape": shape, "shape_source": shape_src,
             "hbm": {"algorithmic_bytes": alg, "bytes_per_cell": alg / N,
                     "achieved_gbs": alg / (ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
                     "frac": alg / (ms * 1e-3) / 1e9 / hbm_peak if hbm_peak else None,
-                    "traffic": traffic, "traffic_over_algorithmic": traffic / alg if traffic else None},
+                    "traffic": traffic, "traffic_over_algorithmic": traffic / alg if traffic else None,
+                    "traffic_by_launch_mode": {m: {"bytes": b, "over_algorithmic": b / alg}
+                                               for m, b in sorted(by_mode.items())} or None,
+                    "traffic_launch_modes": "0: three launches, 128/128/256-cell tiles; 1: cell launch + ordered "
+                                            "face/assembly launch, 64-cell tiles; 2: one ordered launch, 64-cell "
+                                            "tiles"},
             "fp64": fp64_part(stored("linearize", "fp64_inst_per_cell"),
                               stored("linearize", "fp64_warp_inst_per_cell"), N, ms),
             "bound": "alu"}
