@@ -101,3 +101,31 @@ def test_pn_from_natural_matches_oracle(nphase):
     got = grid.pn_from_natural(_T(s.u_new.ravel()), _T(s.flag_new)).cpu().numpy().reshape(nphase + 1, g.N)
     ref = natural_to_pn(g, s.u_new, s.flag_new)
     assert np.allclose(got, ref, rtol=1e-14, atol=0.0)
+
+
+@pytest.mark.parametrize("nphase", [3, 2])
+def test_linearize_pn_is_the_same_for_every_launch_shape(nphase):
+    """The (P, N) path leaves the accumulation out of the cell stage; every
+    launch shape, the one-cluster launch included, gives the same bits."""
+    need_gpu()
+    from paper_2406_10862_gb300 import ocp
+    g, x_new, x_old, dt = _state(7, 5, 4, nphase, 11, 1.001)
+    grid = ocp.Grid(g)
+    shapes = [dict(cells_per_tile=[128, 128, 256], ctas_per_sm=[0, 0, 0], ordered=0),
+              dict(cells_per_tile=[64, 64, 256], ctas_per_sm=[0, 0, 0], ordered=2),
+              dict(cells_per_tile=[32, 32, 32], ctas_per_sm=[0, 0, 0], ordered=3),
+              dict(cells_per_tile=[32, 32, 32], ctas_per_sm=[0, 0, 0], ordered=4)]
+    ref = None
+    for sh in shapes:
+        grid.set_shape(sh)
+        o = grid.linearize_pn(_T(x_new.ravel()), _T(x_old.ravel()), dt, full=True)
+        assert grid.status() == 0, sh
+        got = {k: v.clone() for k, v in o.items()}
+        if ref is None:
+            ref = got
+            continue
+        for k in ref:
+            a, b = got[k], ref[k]
+            if a.dtype == torch.float64:
+                a, b = a.view(torch.int64), b.view(torch.int64)
+            assert torch.equal(a, b), (sh, k)

@@ -158,3 +158,34 @@ def test_newton_pressure_limit_switch_matches_oracle():
     assert ocp.read_controls(c)[0][:3] == (0, 1, 4000.0) and c_ref[0] == (0, 1, 4000.0)
     assert p.cpu().tolist()[0] == 4000.0
     assert np.allclose(u.cpu().numpy().reshape(3, -1), u_ref, rtol=1e-8, atol=1e-9)
+
+
+SHAPES = [dict(cells_per_tile=[128, 128, 256], ctas_per_sm=[0, 0, 0], ordered=0),
+          dict(cells_per_tile=[64, 64, 256], ctas_per_sm=[0, 0, 0], ordered=2),
+          dict(cells_per_tile=[32, 32, 32], ctas_per_sm=[0, 0, 0], ordered=3),
+          dict(cells_per_tile=[32, 32, 32], ctas_per_sm=[0, 0, 0], ordered=4)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%dx%dx%d-np%d-s%d" % c[:5])
+def test_linearize_wells_is_the_same_for_every_launch_shape(case):
+    """The well terms with bottom-hole pressures as unknowns go through the
+    cell stage of every launch shape, including the one-cluster launch that
+    splits a perforated cell's terms over warps: the same bits everywhere."""
+    nx, ny, nz, nphase, seed, p, ctrl = case
+    g, s = W.tiny(nx, ny, nz, nphase=nphase, seed=seed, frac_unsat=0.3 if nphase == 3 else 0.0)
+    ocp, grid = _grid(g)
+    un, fn, uo, fo = dev_state(s)
+    c = ocp.well_controls(ctrl, [0.0, 1e9], grid.device)
+    ref = None
+    for sh in SHAPES:
+        grid.set_shape(sh)
+        out = grid.linearize_wells(un, fn, uo, fo, s.dt, _T(p), c)
+        assert grid.status() == 0, sh
+        npf = grid.nperf * g.nphase
+        got = {k: (v[:npf] if k in ("well_b", "well_c") else v).clone() for k, v in out.items()
+               if isinstance(v, torch.Tensor)}
+        if ref is None:
+            ref = got
+            continue
+        for k in ref:
+            assert torch.equal(got[k].view(torch.int64), ref[k].view(torch.int64)), (sh, k)
