@@ -643,10 +643,11 @@ __device__ __forceinline__ void phase_face(unsigned qa, int lane, unsigned qb, i
   }
 }
 
-// A cell's inputs, loaded by each cell-stage warp before it waits for the
-// PVT table (one round of memory latency).
+// A cell's inputs, loaded by each cell-stage warp while the PVT table's copy
+// is in flight (one round of memory latency; nothing uses them before the
+// wait for the table).
 struct CellIn {
-  double pn, swn, xn, po, swo, xo, phs;
+  double pn, swn, xn, po, swo, xo, phi;
   int fn, fo, ip;
 };
 template <int NB>
@@ -660,7 +661,7 @@ __device__ __forceinline__ void load_cell_in(const ModelArgs& M, long long c, Ce
   in.xo = (NB == 3) ? M.u_old[2 * N + c] : 0.0;
   in.fn = (NB == 3) ? M.f_new[c] : 0;
   in.fo = (NB == 3) ? M.f_old[c] : 0;
-  in.phs = M.phi[c] * M.scale;
+  in.phi = M.phi[c];
   in.ip = M.perf_of_cell[c];
 }
 
@@ -686,7 +687,8 @@ __device__ __forceinline__ void cluster_cell_stage(const ModelArgs& M, const Tab
   const long long c = c0 + lane;
   const bool live = c < N;
   const int ip = (live && w < 4) ? in.ip : -1;
-  const double pn = in.pn, swn = in.swn, phs = in.phs;
+  // pore volume over dt folded into the porosity, as in cell_body
+  const double pn = in.pn, swn = in.swn, phs = in.phi * M.scale;
   const int flag = in.fn & 1;
   const bool tile_well = __any_sync(0xffffffffu, ip >= 0);   // the same in warps 0..3
   Pvt f;
@@ -1007,8 +1009,9 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ModelArg
   const long long c0 = (long long)blockIdx.x * 32;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long c = c0 + lane;
-  // the cell stage's inputs and the face stage's transmissibility, loaded
-  // while the PVT table is on its way
+  // the PVT table's copy first, then the cell stage's inputs and the face
+  // stage's transmissibility while it is on its way
+  table_copy_issue(T, M.table, bar, uses);
   CellIn in{};
   if (w < 4 && c < M.P.N) load_cell_in<NB>(M, c, in);
   double Tf = 0.0;
@@ -1017,7 +1020,7 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ModelArg
     face_task(NB, w, d, ph);
     if (ph >= 0 && c < M.P.N) Tf = M.trans[d * M.P.N + c];
   }
-  load_table(T, M.table, bar, uses, M.status);
+  table_copy_wait(bar, uses, M.status);
   cluster_cell_stage<NB>(M, T, c0, in, buf.cell, S.q, self);
   __syncthreads();                       // the CTA's own quantities and self[] are complete
   cluster_arrive();

@@ -294,8 +294,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
 // its limit records kStatTimeout and waits once more for the copy in flight.
 // Callers that reload the table must make sure no thread still reads the
 // previous one (a barrier before the call).
-__device__ __forceinline__ void load_table(Table& T, const Table* src, unsigned long long& bar, unsigned& uses,
-                                           int* status) {
+// The two halves of load_table, for callers that issue other loads while the
+// copy is in flight: table_copy_issue (thread 0 starts the copy; call it from
+// every thread), then table_copy_wait (every thread).
+__device__ __forceinline__ void table_copy_issue(Table& T, const Table* src, unsigned long long& bar, unsigned uses) {
   const unsigned ubar = (unsigned)__cvta_generic_to_shared(&bar);
   if (threadIdx.x == 0) {
     if (uses == 0) {
@@ -309,12 +311,20 @@ __device__ __forceinline__ void load_table(Table& T, const Table* src, unsigned 
                  "l"(src), "r"((unsigned)sizeof(Table)), "r"(ubar)
                  : "memory");
   }
+}
+__device__ __forceinline__ void table_copy_wait(unsigned long long& bar, unsigned& uses, int* status) {
+  const unsigned ubar = (unsigned)__cvta_generic_to_shared(&bar);
   __syncthreads();                       // the mbarrier is initialised before anyone waits on it
   if (!mbar_wait(ubar, uses & 1u)) {
     atomicOr(status, kStatTimeout);
     mbar_wait(ubar, uses & 1u);
   }
   ++uses;
+}
+__device__ __forceinline__ void load_table(Table& T, const Table* src, unsigned long long& bar, unsigned& uses,
+                                           int* status) {
+  table_copy_issue(T, src, bar, uses);
+  table_copy_wait(bar, uses, status);
 }
 
 // ---------------------------------------------------------------- bit tricks
