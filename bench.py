@@ -1210,7 +1210,7 @@ def run_adjoint(dev, local_rank):
     vjp_ms = e0.elapsed_time(e1) / 20
     vjp_bytes = grid.nnzb * 9 * 8 + 4 * grid.nnzb * 3 + 8 * grid.N * (3 + 9 + 6 + 6 + 1 + 8)
     return {"workload": "history match 100x100x10 (100000 cells), 20 steps of 1 day, checkpoints every 5",
-            "loss": float(loss), "forward_s": t1 - t0, "gradient_s": t2 - t1,
+            "loss": float(loss.detach()), "forward_s": t1 - t0, "gradient_s": t2 - t1,
             "newton_iterations": st.newton_iters, "linear_iterations": st.linear_iters,
             "grad_norm": float(lnk.grad.norm()), "vjp_ms": vjp_ms,
             "vjp_gbs_algorithmic": vjp_bytes / (vjp_ms * 1e-3) / 1e9, "device_status": grid.status()}
